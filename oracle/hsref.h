@@ -1,0 +1,79 @@
+/*
+ * hsref.h -- ORACLE (test infrastructure only).
+ *
+ * Plain, slow, FP64 CPU implementation of the muffin-tin Hamiltonian H and
+ * overlap S of the FLAPW method (Di Napoli, Peise, Hrywniak, Bientinesi,
+ * "High-performance generation of the Hamiltonian and Overlap matrices in
+ * FLAPW methods"). It exists to check the CUDA library and is used only by
+ * the tests, by the smoke check and by the benchmark's CPU-baseline leg. It
+ * shares no code, header, table or constant with the CUDA library.
+ *
+ * Conventions (readings of the paper where it is silent or inconsistent):
+ *  - Y_lm orthonormal with the Condon-Shortley phase, Y_{l,-m} = (-1)^m Y_lm^*.
+ *  - R_a is a proper 3x3 rotation (row-major) acting on column vectors.
+ *  - K = 0: the direction is taken as z; only l = 0 survives.
+ *  - The potential is real: V = sum_{l''} v_{l''} sum_{m''} c_{m''} Y_{l''m''}
+ *    with c_{m''} = 1 (m'' >= 0) and (-1)^{m''} (m'' < 0), so T is Hermitian.
+ *  - Spherical diagonal of T: AA += E_l, BB += E_l ||u_dot_l||^2,
+ *    AB += 1/2, BA += 1/2 (the Hermitian part of the paper's 1 / 0).
+ *  - Matrix index: row t' is the conjugated side, column t the plain side.
+ *  - All complex arrays are interleaved (re, im) doubles.
+ */
+#ifndef HSREF_ORACLE_H
+#define HSREF_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int lmax;
+  double rmt;
+  const double *u, *du, *udot, *dudot; /* [lmax+1] values at rmt           */
+  const double *udot_norm2;            /* [lmax+1] ||u_dot_l||^2            */
+  const double *e_l;                   /* [lmax+1]                          */
+  const double *I_uu, *I_uud, *I_udu, *I_udud; /* [lmax+1][lmax+1][2lmax+1] */
+  const double *T_override; /* NULL, or (2N_L)^2 complex, column-major      */
+} hsref_type;
+
+typedef struct {
+  double omega;
+  int n_types;
+  const hsref_type *types;
+  int n_atoms;
+  const int *type_of_atom;
+  const double *pos; /* [n_atoms][3] Cartesian       */
+  const double *rot; /* [n_atoms][9] row-major       */
+} hsref_system;
+
+/* Spherical Bessel j_l(x) and j_l'(x), l = 0..lmax. */
+int hsref_sbessel(int lmax, double x, double *j, double *dj);
+/* Y_lm(v/|v|) for all l <= lmax, m = -l..l at index l*l + l + m. */
+int hsref_ylm(int lmax, const double *v, double *Y);
+/* Wigner 3j symbol by the Racah formula. */
+double hsref_wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
+/* Gaunt coefficient G_{L,L',L''} = int Y*_{L'} Y_L Y_{L''} dOmega (Eq. gaunt). */
+double hsref_gaunt(int l, int m, int lp, int mp, int lpp, int mpp);
+/* T = [[T^AA, T^AB], [T^BA, T^BB]] (2N_L x 2N_L, column-major) (Eq. t_matrices). */
+int hsref_T(const hsref_type *ty, double *T);
+/* W_a = [A_a; B_a]: out[t][2N_L] (column t contiguous) (Eqs. def_a_tensor/def_b_tensor). */
+int hsref_coefficients(const hsref_system *sys, int atom, int n_g, const double *kvec, double *W);
+/* Full H and S (column-major, leading dimension ld). full=0: upper triangle
+ * only (i <= j), lower part left untouched; full=1: every entry computed.
+ * compensated=1 uses compensated (Dot2) summation for every entry. */
+int hsref_build_HS(const hsref_system *sys, int n_g, const double *kvec, double *H, double *S,
+                   long long ld, int full, int compensated);
+/* Entries H[rows[p], cols[p]] and S[...] only. */
+int hsref_HS_entries(const hsref_system *sys, int n_g, const double *kvec, int n_pairs,
+                     const int *rows, const int *cols, double *H, double *S, int compensated);
+/* The quadruple sum of Eq. def_hamilton / def_overlap with no intermediate
+ * product (tiny inputs only). */
+int hsref_HS_brute(const hsref_system *sys, int n_g, const double *kvec, double *H, double *S,
+                   long long ld);
+/* Number of OpenMP threads the oracle uses. */
+int hsref_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
