@@ -1,0 +1,159 @@
+/*
+ * hsgen.h -- C ABI of the GB300 (sm_103a) muffin-tin H/S generator.
+ *
+ * For one k-point (or a batch of k-points) the library computes the
+ * muffin-tin parts of the FLAPW Hamiltonian H and overlap S of Di Napoli,
+ * Peise, Hrywniak, Bientinesi, "High-performance generation of the
+ * Hamiltonian and Overlap matrices in FLAPW methods":
+ *
+ *   A_{L,a,t}, B_{L,a,t}   matching coefficients          (App. A.1,
+ *                          Eqs. def_a_tensor, def_b_tensor)
+ *   T_a = [[T^AA, T^AB], [T^BA, T^BB]]                     (App. A.2,
+ *                          Eqs. gaunt, nonsph_integrals, t_matrices)
+ *   S = sum_a A_a^H A_a + B_a^H U_a B_a                    (Sec. 4, Eq. S;
+ *                          Eq. def_overlap)
+ *   H = sum_a [A_a;B_a]^H T_a [A_a;B_a]                    (Sec. 4, Eq. H;
+ *                          Eq. def_hamilton)
+ *
+ * Every step runs in CUDA kernels on the device given to hsgen_create.
+ * There is no CPU fallback: without a usable sm_103a device every entry
+ * point that computes returns HSGEN_ECUDA.
+ *
+ * Conventions (readings of the paper where it is silent or inconsistent):
+ *  - Y_lm orthonormal with the Condon-Shortley phase (Y_{l,-m} = (-1)^m Y_lm^*).
+ *  - R_a is a proper rotation acting on column vectors: Y_lm(R_a K^_t).
+ *  - K_t = 0: only l = 0 survives (j_l(0) = delta_l0, |K| j_l'(0) = 0).
+ *  - The potential is real (Eq. pot_harm with coefficient 1 for m'' >= 0 and
+ *    (-1)^{m''} for m'' < 0), so T is Hermitian. The spherical diagonal adds
+ *    E_l to AA, E_l ||u_dot_l||^2 to BB and 1/2 to both AB and BA (the
+ *    Hermitian part of the paper's "1" and "0").
+ *  - U = diag(||u_dot_l||^2) over the B rows (Eq. def_overlap).
+ *  - Matrix entry (t', t): t' is the conjugated (row) side, t the column.
+ *  - Complex numbers are two consecutive doubles (re, im); matrices are
+ *    column-major with a leading dimension (Sec. 4.1 storage format).
+ *
+ * Errors: every function returns a status and never aborts, throws across
+ * the ABI or traps the device; hsgen_last_error() gives the message.
+ * Threading: one context must not be used by two host threads at once, and
+ * calls on one context are ordered (they share device workspaces): issue
+ * them on one stream, or synchronise between streams.
+ */
+#ifndef HSGEN_H
+#define HSGEN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hsgen_ctx hsgen_ctx;
+
+typedef enum {
+  HSGEN_OK = 0,
+  HSGEN_EINVAL = 1,   /* invalid argument (NULL, size, range, layout)          */
+  HSGEN_ENOMEM = 2,   /* device or host allocation failed                      */
+  HSGEN_ECUDA = 3,    /* CUDA runtime/driver error, or no usable sm_103a device */
+  HSGEN_ETIMEOUT = 4, /* a bounded device wait gave up; results are invalid    */
+  HSGEN_ENOTSUP = 5,  /* option combination not supported                      */
+  HSGEN_ENUMERIC = 6  /* |W_l| too small, NaN/Inf input, non-Hermitian T       */
+} hsgen_status;
+
+enum { HSGEN_FP64 = 0, HSGEN_SPLIT = 1 };
+
+typedef struct {
+  int precision;            /* HSGEN_FP64 (default) or HSGEN_SPLIT                  */
+  double target_rel_err;    /* split form: error the slice count is chosen for      */
+                            /* (default 1e-12, relative Frobenius)                  */
+  int slices;               /* split form: slices per operand, 0 = from the target  */
+  int uplo;                 /* 'U' (default): i <= j written; 'L': i >= j written   */
+  int fill_full;            /* 1: also write the other triangle (Hermitian mirror)  */
+  int atom_chunk;           /* atoms per pass over the depth, 0 = all at once       */
+  long long wait_timeout_ns; /* limit of every device-side wait (default 2e9)       */
+} hsgen_options;
+
+/* Radial data of one atom species (App. A.1 and A.2). All arrays are host
+ * pointers, read during hsgen_set_atoms and copied; the caller keeps
+ * ownership. Index of I: ((l * (lmax+1)) + l') * (2 lmax + 1) + l'', with
+ * I^{(x,y)}_{l,l',l''} = int x_{l'} v_{l''} y_l r^2 dr (Eq. nonsph_integrals). */
+typedef struct {
+  int lmax;                         /* 0..10                                   */
+  double rmt;                       /* muffin-tin radius r_MT (> 0)            */
+  const double *u, *du;             /* [lmax+1] u_l(r_MT), u_l'(r_MT)          */
+  const double *udot, *dudot;       /* [lmax+1] u_dot_l(r_MT), u_dot_l'(r_MT)  */
+  const double *wronskian;          /* [lmax+1] W_l, or NULL: computed as      */
+                                    /* u_dot u' - u u_dot' (App. A.1)          */
+  const double *udot_norm2;         /* [lmax+1] ||u_dot_l||^2 (> 0)            */
+  const double *e_l;                /* [lmax+1] E_l                            */
+  const double *I_uu, *I_uud;       /* I^{(u,u)}, I^{(u,u_dot)}                */
+  const double *I_udu, *I_udud;     /* I^{(u_dot,u)}, I^{(u_dot,u_dot)}        */
+  const double *T_override;         /* NULL, or (2N_L)^2 complex, column-major */
+                                    /* Hermitian T used instead of Eq.         */
+                                    /* t_matrices (rows/cols: A then B)        */
+} hsgen_type;
+
+typedef struct {
+  double ms_coefficients;  /* a1: radial factors + A/B coefficient kernel      */
+  double ms_tapply;        /* a3: X = T W                                       */
+  double ms_slice;         /* a5: split-form slicing (0 for FP64)               */
+  double ms_contract;      /* a4/a5: H and S contraction                        */
+  double ms_total;         /* whole last call, device time                      */
+  double flops_algorithmic;/* algorithmic flops of the last call (all k-points) */
+  int precision;           /* form used by the last call                        */
+  int slices;              /* slices per operand used (split form)              */
+  int n_kpoints;           /* k-points in the last call                         */
+  long long workspace_bytes; /* device workspace currently held                 */
+} hsgen_stats;
+
+/* Fills *opt with the defaults listed above. */
+hsgen_status hsgen_default_options(hsgen_options *opt);
+
+/* Creates a context on CUDA device `cuda_device` (must be sm_103). opt may be
+ * NULL (defaults). *out receives the context, NULL on failure. */
+hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options *opt);
+
+/* Sets the crystal (Sec. 2.2, App. A.1): lattice rows a1,a2,a3 in bohr
+ * (lattice[9], row-major), cell volume omega (> 0), the species and the atoms
+ * (type_of_atom[n_atoms] in [0,n_types), pos[n_atoms][3] Cartesian,
+ * rot[n_atoms][9] row-major proper rotations). Host pointers, deep-copied.
+ * Assembles the T matrices on the device (a2). Synchronous. */
+hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega, int n_types,
+                             const hsgen_type *types, int n_atoms, const int *type_of_atom,
+                             const double *pos, const double *rot);
+
+/* Builds H and S for one k-point: kvec[n_g][3] are the Cartesian vectors
+ * K_t = k + G_t (host or device pointer). H and S are complex128 column-major
+ * n_g x n_g with leading dimension ld >= n_g: device pointers (written
+ * asynchronously on `cuda_stream`, a cudaStream_t or NULL for the default
+ * stream) or host pointers (the library copies into them and the call
+ * returns after the copy). Only the triangle named by opt.uplo is written
+ * unless opt.fill_full; diagonal imaginary parts are set to 0. */
+hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
+                            void *cuda_stream);
+
+/* Builds H and S for n_k k-points in one go (D22: one H,S per k-point):
+ * n_g[k], kvec[k] (host pointers to [n_g[k]][3]), H[k], S[k] device
+ * pointers with leading dimension ld[k]. All k-points' contraction tiles run
+ * in one persistent launch over a grouped tile queue. */
+hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec,
+                                    void *const *H, void *const *S, const long long *ld, void *cuda_stream);
+
+/* Inspection of single steps (same kernels as hsgen_build_HS):
+ * W = [A_a; B_a] stacked over atoms (a1) into W (device, complex, column t at
+ * W + t*ldw, rows at the offsets hsgen_depth_layout reports, padding rows 0). */
+hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, void *W, long long ldw,
+                                void *cuda_stream);
+/* T of species `type` (a2) copied into T (host, (2N_L)^2 complex, column-major). */
+hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T);
+/* Row offsets of the atoms in the depth of W (offsets[n_atoms+1], host); the
+ * block of atom a is offsets[a] .. offsets[a] + 2 N_La (A rows, then B rows),
+ * followed by zero rows up to offsets[a+1]. */
+hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
+
+hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *stats);
+const char *hsgen_last_error(const hsgen_ctx *ctx);
+/* Releases the context and its device memory. NULL-safe. */
+void hsgen_destroy(hsgen_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSGEN_H */

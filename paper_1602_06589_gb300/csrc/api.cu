@@ -1,0 +1,625 @@
+// api.cu -- the C ABI of include/hsgen.h: argument checks, context state,
+// device workspaces and the order of kernel launches for one k-point:
+//
+//   a0/a1 radial factors + coefficient kernel  -> W = [A_a; B_a] stacked
+//   a3    X_a = T_a W_a per atom
+//   a4    H = W^H X, S = W^H diag(u) W (one triangle)      (FP64 form)
+//   a5    slice W, X, diag(u) W; tcgen05 split products    (split form)
+//   a6    steps a1-a5 repeated per chunk of atoms, accumulating into H, S
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "split.cuh"
+
+namespace hsg {
+
+hsgen_status set_err(hsgen_ctx *ctx, hsgen_status st, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+hsgen_status cuda_err(hsgen_ctx *ctx, cudaError_t e, const char *what) {
+  std::string m = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return set_err(ctx, HSGEN_ENOMEM, m);
+  return set_err(ctx, HSGEN_ECUDA, m);
+}
+
+static bool finite_all(const double *p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes) {
+  if (w.bytes >= bytes) return HSGEN_OK;
+  if (w.ptr) {
+    cudaError_t e = cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.bytes = 0;
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaFree(workspace)");
+  }
+  cudaError_t e = cudaMalloc(&w.ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_err(ctx, e, "cudaMalloc(workspace)");
+  }
+  w.bytes = bytes;
+  return HSGEN_OK;
+}
+
+static void free_system(hsgen_ctx *ctx) {
+  for (auto &sp : ctx->types)
+    if (sp.d_T) cudaFree(sp.d_T);
+  ctx->types.clear();
+  cudaFree(ctx->d_toa);
+  cudaFree(ctx->d_off);
+  cudaFree(ctx->d_atoms_by_type);
+  cudaFree(ctx->d_pos);
+  cudaFree(ctx->d_rot);
+  cudaFree(ctx->d_urow);
+  cudaFree(ctx->d_radial);
+  ctx->d_toa = ctx->d_off = ctx->d_atoms_by_type = nullptr;
+  ctx->d_pos = ctx->d_rot = ctx->d_urow = nullptr;
+  ctx->d_radial = nullptr;
+  ctx->have_system = false;
+}
+
+// Chunks of atoms [a0, a1) processed per pass over the depth (a6).
+static std::vector<std::pair<int, int>> atom_chunks(const hsgen_ctx *ctx) {
+  int na = (int)ctx->toa.size();
+  int c = ctx->opt.atom_chunk > 0 ? ctx->opt.atom_chunk : na;
+  std::vector<std::pair<int, int>> out;
+  for (int a = 0; a < na; a += c) out.push_back({a, std::min(na, a + c)});
+  return out;
+}
+
+}  // namespace hsg
+
+using namespace hsg;
+
+extern "C" {
+
+hsgen_status hsgen_default_options(hsgen_options *opt) {
+  if (!opt) return HSGEN_EINVAL;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = HSGEN_FP64;
+  opt->target_rel_err = 1e-12;
+  opt->slices = 0;
+  opt->uplo = 'U';
+  opt->fill_full = 0;
+  opt->atom_chunk = 0;
+  opt->wait_timeout_ns = 2000000000LL;
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options *opt) {
+  if (!out) return HSGEN_EINVAL;
+  *out = nullptr;
+  hsgen_options o;
+  hsgen_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != HSGEN_FP64 && o.precision != HSGEN_SPLIT) return HSGEN_EINVAL;
+  if (o.uplo != 'U' && o.uplo != 'L') return HSGEN_EINVAL;
+  if (o.atom_chunk < 0 || o.slices < 0 || o.slices > kMaxSlices) return HSGEN_EINVAL;
+  if (!(o.target_rel_err > 0.0) || o.wait_timeout_ns <= 0) return HSGEN_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return HSGEN_ECUDA;
+  }
+  if (cuda_device < 0 || cuda_device >= ndev) return HSGEN_EINVAL;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, cuda_device) != cudaSuccess) return HSGEN_ECUDA;
+  if (prop.major != 10 || prop.minor != 3) return HSGEN_ECUDA;  // built for sm_103a only
+  hsgen_ctx *ctx = new (std::nothrow) hsgen_ctx();
+  if (!ctx) return HSGEN_ENOMEM;
+  ctx->device = cuda_device;
+  ctx->opt = o;
+  if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess) {
+    delete ctx;
+    return HSGEN_ECUDA;
+  }
+  for (auto &e : ctx->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      delete ctx;
+      return HSGEN_ECUDA;
+    }
+  ctx->events_ready = true;
+  *out = ctx;
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega, int n_types,
+                             const hsgen_type *types, int n_atoms, const int *type_of_atom, const double *pos,
+                             const double *rot) {
+  if (!ctx) return HSGEN_EINVAL;
+  if (!lattice || !types || !type_of_atom || !pos || !rot)
+    return set_err(ctx, HSGEN_EINVAL, "set_atoms: NULL argument");
+  if (n_types <= 0 || n_atoms <= 0) return set_err(ctx, HSGEN_EINVAL, "set_atoms: n_types and n_atoms must be > 0");
+  if (!(omega > 0.0) || !std::isfinite(omega)) return set_err(ctx, HSGEN_EINVAL, "set_atoms: omega must be > 0");
+  if (!finite_all(lattice, 9) || !finite_all(pos, 3 * (size_t)n_atoms) || !finite_all(rot, 9 * (size_t)n_atoms))
+    return set_err(ctx, HSGEN_ENUMERIC, "set_atoms: non-finite lattice, position or rotation");
+  for (int a = 0; a < n_atoms; ++a)
+    if (type_of_atom[a] < 0 || type_of_atom[a] >= n_types)
+      return set_err(ctx, HSGEN_EINVAL, "set_atoms: type_of_atom out of range");
+  std::vector<Species> sps(n_types);
+  for (int t = 0; t < n_types; ++t) {
+    const hsgen_type &ty = types[t];
+    if (ty.lmax < 0 || ty.lmax > kLmaxMax) return set_err(ctx, HSGEN_EINVAL, "set_atoms: lmax must be in 0..10");
+    if (!(ty.rmt > 0.0)) return set_err(ctx, HSGEN_EINVAL, "set_atoms: rmt must be > 0");
+    if (!ty.u || !ty.du || !ty.udot || !ty.dudot || !ty.udot_norm2 || !ty.e_l)
+      return set_err(ctx, HSGEN_EINVAL, "set_atoms: NULL radial array");
+    if (!ty.T_override && (!ty.I_uu || !ty.I_uud || !ty.I_udu || !ty.I_udud))
+      return set_err(ctx, HSGEN_EINVAL, "set_atoms: NULL radial integrals");
+    Species &sp = sps[t];
+    int n1 = ty.lmax + 1;
+    sp.lmax = ty.lmax;
+    sp.nl = n1 * n1;
+    sp.dpad = round_up(2 * sp.nl, 8);
+    sp.rmt = ty.rmt;
+    sp.u.assign(ty.u, ty.u + n1);
+    sp.du.assign(ty.du, ty.du + n1);
+    sp.udot.assign(ty.udot, ty.udot + n1);
+    sp.dudot.assign(ty.dudot, ty.dudot + n1);
+    sp.un2.assign(ty.udot_norm2, ty.udot_norm2 + n1);
+    sp.el.assign(ty.e_l, ty.e_l + n1);
+    if (!finite_all(sp.u.data(), n1) || !finite_all(sp.du.data(), n1) || !finite_all(sp.udot.data(), n1) ||
+        !finite_all(sp.dudot.data(), n1) || !finite_all(sp.un2.data(), n1) || !finite_all(sp.el.data(), n1) ||
+        !std::isfinite(ty.rmt))
+      return set_err(ctx, HSGEN_ENUMERIC, "set_atoms: non-finite radial data");
+    sp.wr.resize(n1);
+    for (int l = 0; l < n1; ++l) {
+      sp.wr[l] = ty.wronskian ? ty.wronskian[l] : sp.udot[l] * sp.du[l] - sp.u[l] * sp.dudot[l];
+      if (!std::isfinite(sp.wr[l]) || std::fabs(sp.wr[l]) < 1e-12)
+        return set_err(ctx, HSGEN_ENUMERIC, "set_atoms: Wronskian |W_l| below 1e-12");
+      if (!(sp.un2[l] > 0.0)) return set_err(ctx, HSGEN_EINVAL, "set_atoms: udot_norm2 must be > 0");
+    }
+    size_t nI = (size_t)n1 * n1 * (2 * ty.lmax + 1);
+    if (ty.T_override) {
+      int n = 2 * sp.nl;
+      sp.T_override.assign(ty.T_override, ty.T_override + 2 * (size_t)n * n);
+      if (!finite_all(sp.T_override.data(), sp.T_override.size()))
+        return set_err(ctx, HSGEN_ENUMERIC, "set_atoms: non-finite T_override");
+      double mx = 0.0, dev = 0.0;
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+          const double *x = &sp.T_override[2 * (r + (size_t)c * n)];
+          const double *y = &sp.T_override[2 * (c + (size_t)r * n)];
+          mx = std::max(mx, std::hypot(x[0], x[1]));
+          dev = std::max(dev, std::hypot(x[0] - y[0], x[1] + y[1]));
+        }
+      if (dev > 1e-12 * std::max(mx, 1e-300))
+        return set_err(ctx, HSGEN_ENUMERIC, "set_atoms: T_override is not Hermitian");
+    } else {
+      const double *I[4] = {ty.I_uu, ty.I_uud, ty.I_udu, ty.I_udud};
+      for (int k = 0; k < 4; ++k) {
+        sp.I[k].assign(I[k], I[k] + nI);
+        if (!finite_all(sp.I[k].data(), nI)) return set_err(ctx, HSGEN_ENUMERIC, "set_atoms: non-finite I");
+      }
+    }
+  }
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  free_system(ctx);
+  ctx->types = std::move(sps);
+  std::memcpy(ctx->lattice, lattice, sizeof(ctx->lattice));
+  ctx->omega = omega;
+  ctx->toa.assign(type_of_atom, type_of_atom + n_atoms);
+  ctx->pos.assign(pos, pos + 3 * (size_t)n_atoms);
+  ctx->rot.assign(rot, rot + 9 * (size_t)n_atoms);
+  ctx->off.assign(n_atoms + 1, 0);
+  for (int a = 0; a < n_atoms; ++a) ctx->off[a + 1] = ctx->off[a] + ctx->types[ctx->toa[a]].dpad;
+  ctx->depth = ctx->off[n_atoms];
+  // per depth row weight u (A rows 1, B rows ||u_dot_l||^2, padding 0)
+  std::vector<double> urow(ctx->depth, 0.0);
+  for (int a = 0; a < n_atoms; ++a) {
+    const Species &sp = ctx->types[ctx->toa[a]];
+    for (int l = 0; l <= sp.lmax; ++l)
+      for (int m = -l; m <= l; ++m) {
+        int L = l * l + l + m;
+        urow[ctx->off[a] + L] = 1.0;
+        urow[ctx->off[a] + sp.nl + L] = sp.un2[l];
+      }
+  }
+  // atom lists grouped by species
+  ctx->atoms_of_type.assign(n_types, {});
+  for (int a = 0; a < n_atoms; ++a) ctx->atoms_of_type[ctx->toa[a]].push_back(a);
+  std::vector<int> flat;
+  ctx->atoms_by_type_start.assign(n_types + 1, 0);
+  for (int t = 0; t < n_types; ++t) {
+    ctx->atoms_by_type_start[t] = (int)flat.size();
+    flat.insert(flat.end(), ctx->atoms_of_type[t].begin(), ctx->atoms_of_type[t].end());
+  }
+  ctx->atoms_by_type_start[n_types] = (int)flat.size();
+  std::vector<RadialParams> rp(n_types);
+  for (int t = 0; t < n_types; ++t) {
+    const Species &sp = ctx->types[t];
+    std::memset(&rp[t], 0, sizeof(RadialParams));
+    rp[t].lmax = sp.lmax;
+    rp[t].rmt = sp.rmt;
+    for (int l = 0; l <= sp.lmax; ++l) {
+      rp[t].u[l] = sp.u[l];
+      rp[t].du[l] = sp.du[l];
+      rp[t].udot[l] = sp.udot[l];
+      rp[t].dudot[l] = sp.dudot[l];
+      rp[t].pre[l] = 4.0 * M_PI / (sp.wr[l] * std::sqrt(omega));
+    }
+  }
+  HSG_CUDA(ctx, cudaMalloc(&ctx->d_toa, sizeof(int) * n_atoms));
+  HSG_CUDA(ctx, cudaMalloc(&ctx->d_off, sizeof(int) * (n_atoms + 1)));
+  HSG_CUDA(ctx, cudaMalloc(&ctx->d_atoms_by_type, sizeof(int) * n_atoms));
+  HSG_CUDA(ctx, cudaMalloc(&ctx->d_pos, sizeof(double) * 3 * n_atoms));
+  HSG_CUDA(ctx, cudaMalloc(&ctx->d_rot, sizeof(double) * 9 * n_atoms));
+  HSG_CUDA(ctx, cudaMalloc(&ctx->d_urow, sizeof(double) * std::max(ctx->depth, 1)));
+  HSG_CUDA(ctx, cudaMalloc(&ctx->d_radial, sizeof(RadialParams) * n_types));
+  HSG_CUDA(ctx, cudaMemcpy(ctx->d_toa, ctx->toa.data(), sizeof(int) * n_atoms, cudaMemcpyHostToDevice));
+  HSG_CUDA(ctx, cudaMemcpy(ctx->d_off, ctx->off.data(), sizeof(int) * (n_atoms + 1), cudaMemcpyHostToDevice));
+  HSG_CUDA(ctx, cudaMemcpy(ctx->d_atoms_by_type, flat.data(), sizeof(int) * n_atoms, cudaMemcpyHostToDevice));
+  HSG_CUDA(ctx, cudaMemcpy(ctx->d_pos, ctx->pos.data(), sizeof(double) * 3 * n_atoms, cudaMemcpyHostToDevice));
+  HSG_CUDA(ctx, cudaMemcpy(ctx->d_rot, ctx->rot.data(), sizeof(double) * 9 * n_atoms, cudaMemcpyHostToDevice));
+  HSG_CUDA(ctx, cudaMemcpy(ctx->d_urow, urow.data(), sizeof(double) * ctx->depth, cudaMemcpyHostToDevice));
+  HSG_CUDA(ctx, cudaMemcpy(ctx->d_radial, rp.data(), sizeof(RadialParams) * n_types, cudaMemcpyHostToDevice));
+  // a2: T matrices on the device
+  size_t scratch = 0;
+  for (auto &sp : ctx->types) {
+    size_t nI = (size_t)(sp.lmax + 1) * (sp.lmax + 1) * (2 * sp.lmax + 1);
+    int nq = 2 * sp.lmax + 2;
+    scratch = std::max(scratch, sizeof(double) * (2 * nq + 4 * nI + 2 * (sp.lmax + 1) + (size_t)nq * kLTab * kLTab));
+  }
+  double *d_scratch = nullptr;
+  HSG_CUDA(ctx, cudaMalloc(&d_scratch, scratch));
+  for (auto &sp : ctx->types) {
+    cudaError_t e = cudaMalloc(&sp.d_T, sizeof(double2) * (size_t)sp.dpad * sp.dpad);
+    if (e == cudaSuccess) e = launch_tmatrix(sp, (double2 *)sp.d_T, d_scratch, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+      cudaFree(d_scratch);
+      return cuda_err(ctx, e, "T-matrix assembly");
+    }
+  }
+  HSG_CUDA(ctx, cudaFree(d_scratch));
+  ctx->have_system = true;
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity) {
+  if (!ctx || !offsets) return HSGEN_EINVAL;
+  if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "depth_layout: no system set");
+  if (capacity < (int)ctx->off.size()) return set_err(ctx, HSGEN_EINVAL, "depth_layout: capacity too small");
+  std::memcpy(offsets, ctx->off.data(), sizeof(int) * ctx->off.size());
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T) {
+  if (!ctx || !T) return HSGEN_EINVAL;
+  if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "T_matrix: no system set");
+  if (type < 0 || type >= (int)ctx->types.size()) return set_err(ctx, HSGEN_EINVAL, "T_matrix: bad type");
+  const Species &sp = ctx->types[type];
+  int n = 2 * sp.nl;
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  HSG_CUDA(ctx, cudaMemcpy2D(T, sizeof(double2) * n, sp.d_T, sizeof(double2) * sp.dpad, sizeof(double2) * n, n,
+                             cudaMemcpyDeviceToHost));
+  return HSGEN_OK;
+}
+
+}  // extern "C"
+
+namespace hsg {
+
+struct KpointJob {
+  int n_g;
+  const double *kvec_dev;
+  double2 *H, *S;
+  long long ld;
+};
+
+// Device workspace layout for one k-point (byte offsets).
+struct WsLayout {
+  size_t kvec, F, W, X, split, total;
+  long long ldw;
+};
+
+static WsLayout ws_layout(const hsgen_ctx *ctx, int n_g, int chunk_depth, bool split, int slices) {
+  WsLayout L;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t r = o;
+    o += (b + 255) / 256 * 256;
+    return r;
+  };
+  L.ldw = chunk_depth;
+  L.kvec = take(sizeof(double) * 3 * (size_t)n_g);
+  L.F = take(sizeof(double2) * (size_t)ctx->types.size() * n_g * kRadStride);
+  L.W = take(sizeof(double2) * (size_t)chunk_depth * n_g);
+  L.X = take(sizeof(double2) * (size_t)chunk_depth * n_g);
+  L.split = split ? take(split_workspace_bytes(n_g, chunk_depth, slices)) : o;
+  L.total = o;
+  return L;
+}
+
+static int max_chunk_depth(const hsgen_ctx *ctx) {
+  int d = 0;
+  for (auto c : atom_chunks(ctx)) d = std::max(d, ctx->off[c.second] - ctx->off[c.first]);
+  return d;
+}
+
+// The whole path for one k-point on stream s; kvec on the device.
+static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_t s, char *ws, const WsLayout &L,
+                               bool record) {
+  const int n_g = job.n_g;
+  const int nt = (int)ctx->types.size();
+  double2 *F = (double2 *)(ws + L.F);
+  double2 *W = (double2 *)(ws + L.W);
+  double2 *X = (double2 *)(ws + L.X);
+  const bool split = ctx->opt.precision == HSGEN_SPLIT;
+  auto chunks = atom_chunks(ctx);
+  const bool single = chunks.size() == 1;
+  if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
+  HSG_CUDA(ctx, launch_radial(n_g, job.kvec_dev, nt, ctx->d_radial, F, s));
+  int slices = split ? choose_slices(ctx->opt.target_rel_err, ctx->opt.slices) : 0;
+  for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    int a0 = chunks[ci].first, a1 = chunks[ci].second;
+    int row_base = ctx->off[a0];
+    int cdepth = ctx->off[a1] - row_base;
+    for (int t = 0; t < nt; ++t) {
+      // atoms of species t inside [a0, a1): contiguous range of the per-species list
+      const auto &lst = ctx->atoms_of_type[t];
+      int lo = 0, hi = 0;
+      while (lo < (int)lst.size() && lst[lo] < a0) ++lo;
+      hi = lo;
+      while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
+      if (hi == lo) continue;
+      const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
+      HSG_CUDA(ctx, launch_coefficients(ctx->types[t].lmax, n_g, job.kvec_dev, F + (size_t)t * n_g * kRadStride,
+                                        d_atoms, hi - lo, ctx->d_pos, ctx->d_rot, ctx->d_off, row_base,
+                                        ctx->types[t].dpad, W, L.ldw, s));
+    }
+    if (record && single) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
+    for (int t = 0; t < nt; ++t) {
+      const auto &lst = ctx->atoms_of_type[t];
+      int lo = 0, hi = 0;
+      while (lo < (int)lst.size() && lst[lo] < a0) ++lo;
+      hi = lo;
+      while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
+      if (hi == lo) continue;
+      const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
+      if (split) {
+        SplitCtx sc{ctx->opt.wait_timeout_ns};
+        hsgen_status st = split_tapply(ctx, sc, ctx->types[t], d_atoms, hi - lo, ctx->d_off, row_base, n_g, W, X,
+                                       L.ldw, ws + L.split, slices, s);
+        if (st != HSGEN_OK) return st;
+      } else {
+        HSG_CUDA(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].d_T, d_atoms,
+                                         hi - lo, ctx->d_off, row_base, W, X, L.ldw, s));
+      }
+    }
+    if (record && single) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+    if (split) {
+      SplitCtx sc{ctx->opt.wait_timeout_ns};
+      hsgen_status st = split_hs(ctx, sc, n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H, job.S, job.ld,
+                                 ctx->opt.uplo, ci > 0, ws + L.split, slices, s, record && single ? ctx->ev[3] : nullptr);
+      if (st != HSGEN_OK) return st;
+    } else {
+      if (record && single) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
+      HSG_CUDA(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H, job.S, job.ld,
+                                   ctx->opt.uplo, ci > 0 ? 1 : 0, s));
+    }
+  }
+  if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
+  if (ctx->opt.fill_full) {
+    HSG_CUDA(ctx, launch_mirror(n_g, job.H, job.ld, ctx->opt.uplo, s));
+    HSG_CUDA(ctx, launch_mirror(n_g, job.S, job.ld, ctx->opt.uplo, s));
+  }
+  if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
+  ctx->stats.slices = slices;
+  return HSGEN_OK;
+}
+
+static double algorithmic_flops(const hsgen_ctx *ctx, int n_g) {
+  double depth = 0.0, t = 0.0;
+  for (int a : ctx->toa) {
+    double nl = ctx->types[a].nl;
+    depth += 2.0 * nl;
+    t += 4.0 * nl * nl;
+  }
+  (void)t;
+  double tri = (double)n_g * (n_g + 1) / 2.0;
+  double ft = 0.0;
+  for (int a : ctx->toa) ft += 8.0 * n_g * 4.0 * ctx->types[a].nl * ctx->types[a].nl;
+  return 16.0 * tri * depth + ft;
+}
+
+static hsgen_status check_kvec(hsgen_ctx *ctx, int n_g, const double *kvec_host) {
+  if (!kvec_host) return HSGEN_OK;
+  if (!finite_all(kvec_host, 3 * (size_t)n_g)) return set_err(ctx, HSGEN_ENUMERIC, "build: non-finite kvec");
+  return HSGEN_OK;
+}
+
+}  // namespace hsg
+
+extern "C" {
+
+hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, void *W, long long ldw,
+                                void *cuda_stream) {
+  if (!ctx) return HSGEN_EINVAL;
+  if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "coefficients: no system set");
+  if (n_g < 0 || !kvec || !W) return set_err(ctx, HSGEN_EINVAL, "coefficients: bad argument");
+  if (ldw < ctx->depth) return set_err(ctx, HSGEN_EINVAL, "coefficients: ldw < depth");
+  if (n_g == 0) return HSGEN_OK;
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  bool kdev = is_device_ptr(kvec);
+  if (!kdev) {
+    hsgen_status st = check_kvec(ctx, n_g, kvec);
+    if (st != HSGEN_OK) return st;
+  }
+  if (!is_device_ptr(W)) return set_err(ctx, HSGEN_EINVAL, "coefficients: W must be a device pointer");
+  WsLayout L = ws_layout(ctx, n_g, 0, false, 0);
+  hsgen_status st = ensure_ws(ctx, ctx->ws_main, L.total);
+  if (st != HSGEN_OK) return st;
+  char *ws = (char *)ctx->ws_main.ptr;
+  const double *kd = kvec;
+  if (!kdev) {
+    HSG_CUDA(ctx, cudaMemcpyAsync(ws + L.kvec, kvec, sizeof(double) * 3 * n_g, cudaMemcpyHostToDevice, s));
+    kd = (const double *)(ws + L.kvec);
+  }
+  double2 *F = (double2 *)(ws + L.F);
+  HSG_CUDA(ctx, launch_radial(n_g, kd, (int)ctx->types.size(), ctx->d_radial, F, s));
+  for (int t = 0; t < (int)ctx->types.size(); ++t) {
+    int n = (int)ctx->atoms_of_type[t].size();
+    if (!n) continue;
+    HSG_CUDA(ctx, launch_coefficients(ctx->types[t].lmax, n_g, kd, F + (size_t)t * n_g * kRadStride,
+                                      ctx->d_atoms_by_type + ctx->atoms_by_type_start[t], n, ctx->d_pos, ctx->d_rot,
+                                      ctx->d_off, 0, ctx->types[t].dpad, (double2 *)W, ldw, s));
+  }
+  if (!kdev) HSG_CUDA(ctx, cudaStreamSynchronize(s));
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
+                            void *cuda_stream) {
+  if (!ctx) return HSGEN_EINVAL;
+  if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "build_HS: no system set");
+  if (n_g < 0) return set_err(ctx, HSGEN_EINVAL, "build_HS: n_g < 0");
+  if (n_g == 0) return HSGEN_OK;
+  if (!kvec || !H || !S) return set_err(ctx, HSGEN_EINVAL, "build_HS: NULL pointer");
+  if (ld < n_g) return set_err(ctx, HSGEN_EINVAL, "build_HS: ld < n_g");
+  if (H == S) return set_err(ctx, HSGEN_EINVAL, "build_HS: H and S alias");
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  bool kdev = is_device_ptr(kvec);
+  if (!kdev) {
+    hsgen_status st = check_kvec(ctx, n_g, kvec);
+    if (st != HSGEN_OK) return st;
+  }
+  bool hdev = is_device_ptr(H), sdev = is_device_ptr(S);
+  if (hdev != sdev) return set_err(ctx, HSGEN_EINVAL, "build_HS: H and S must both be device or both host");
+  bool split = ctx->opt.precision == HSGEN_SPLIT;
+  int slices = split ? choose_slices(ctx->opt.target_rel_err, ctx->opt.slices) : 0;
+  WsLayout L = ws_layout(ctx, n_g, max_chunk_depth(ctx), split, slices);
+  hsgen_status st = ensure_ws(ctx, ctx->ws_main, L.total);
+  if (st != HSGEN_OK) return st;
+  char *ws = (char *)ctx->ws_main.ptr;
+  KpointJob job;
+  job.n_g = n_g;
+  job.ld = ld;
+  job.kvec_dev = kvec;
+  if (!kdev) {
+    HSG_CUDA(ctx, cudaMemcpyAsync(ws + L.kvec, kvec, sizeof(double) * 3 * n_g, cudaMemcpyHostToDevice, s));
+    job.kvec_dev = (const double *)(ws + L.kvec);
+  }
+  size_t hs_bytes = sizeof(double2) * (size_t)ld * n_g;
+  if (hdev) {
+    job.H = (double2 *)H;
+    job.S = (double2 *)S;
+  } else {
+    st = ensure_ws(ctx, ctx->ws_out, 2 * hs_bytes);
+    if (st != HSGEN_OK) return st;
+    job.H = (double2 *)ctx->ws_out.ptr;
+    job.S = (double2 *)((char *)ctx->ws_out.ptr + hs_bytes);
+    // untouched triangle of a host output keeps its previous contents
+    HSG_CUDA(ctx, cudaMemcpyAsync(job.H, H, hs_bytes, cudaMemcpyHostToDevice, s));
+    HSG_CUDA(ctx, cudaMemcpyAsync(job.S, S, hs_bytes, cudaMemcpyHostToDevice, s));
+  }
+  st = run_kpoint(ctx, job, s, ws, L, true);
+  if (st != HSGEN_OK) return st;
+  if (!hdev) {
+    HSG_CUDA(ctx, cudaMemcpyAsync(H, job.H, hs_bytes, cudaMemcpyDeviceToHost, s));
+    HSG_CUDA(ctx, cudaMemcpyAsync(S, job.S, hs_bytes, cudaMemcpyDeviceToHost, s));
+  }
+  if (split) {
+    st = split_check_status(ctx, s);
+    if (st != HSGEN_OK) return st;
+  }
+  if (!hdev || !kdev) HSG_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->stats.precision = ctx->opt.precision;
+  ctx->stats.n_kpoints = 1;
+  ctx->stats.flops_algorithmic = algorithmic_flops(ctx, n_g);
+  ctx->phase_used[0] = atom_chunks(ctx).size() == 1;
+  ctx->phase_used[1] = 1;
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec,
+                                    void *const *H, void *const *S, const long long *ld, void *cuda_stream) {
+  if (!ctx) return HSGEN_EINVAL;
+  if (n_k < 0 || (n_k > 0 && (!n_g || !kvec || !H || !S || !ld)))
+    return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: bad argument");
+  double flops = 0.0;
+  for (int k = 0; k < n_k; ++k) {
+    if (n_g[k] > 0 && !is_device_ptr(H[k]))
+      return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: H, S must be device pointers");
+  }
+  hsgen_status st = split_batched(ctx, n_k, n_g, kvec, H, S, ld, (cudaStream_t)cuda_stream);
+  if (st != HSGEN_ENOTSUP) {
+    if (st == HSGEN_OK) {
+      for (int k = 0; k < n_k; ++k) flops += algorithmic_flops(ctx, n_g[k]);
+      ctx->stats.flops_algorithmic = flops;
+      ctx->stats.n_kpoints = n_k;
+    }
+    return st;
+  }
+  for (int k = 0; k < n_k; ++k) {
+    st = hsgen_build_HS(ctx, n_g[k], kvec[k], H[k], S[k], ld[k], cuda_stream);
+    if (st != HSGEN_OK) return st;
+    flops += algorithmic_flops(ctx, n_g[k]);
+  }
+  ctx->stats.flops_algorithmic = flops;
+  ctx->stats.n_kpoints = n_k;
+  ctx->phase_used[0] = 0;
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
+  if (!ctx || !out) return HSGEN_EINVAL;
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  hsgen_stats st = ctx->stats;
+  st.ms_coefficients = st.ms_tapply = st.ms_slice = st.ms_contract = st.ms_total = 0.0;
+  if (ctx->phase_used[1]) {
+    float ms = 0.f;
+    HSG_CUDA(ctx, cudaEventSynchronize(ctx->ev[5]));
+    if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]) == cudaSuccess) st.ms_total = ms;
+    if (ctx->phase_used[0]) {
+      if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st.ms_coefficients = ms;
+      if (cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) == cudaSuccess) st.ms_tapply = ms;
+      if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) == cudaSuccess) st.ms_slice = ms;
+      if (cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]) == cudaSuccess) st.ms_contract = ms;
+    }
+    cudaGetLastError();
+  }
+  st.workspace_bytes = (long long)(ctx->ws_main.bytes + ctx->ws_out.bytes);
+  *out = st;
+  return HSGEN_OK;
+}
+
+const char *hsgen_last_error(const hsgen_ctx *ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void hsgen_destroy(hsgen_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  free_system(ctx);
+  split_release(ctx);
+  if (ctx->ws_main.ptr) cudaFree(ctx->ws_main.ptr);
+  if (ctx->ws_out.ptr) cudaFree(ctx->ws_out.ptr);
+  if (ctx->events_ready)
+    for (auto &e : ctx->ev) cudaEventDestroy(e);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// internal.cuh -- shared declarations of the hsgen CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hsgen.h"
+
+namespace hsg {
+
+constexpr int kLmaxMax = 10;                    // largest l_max per species
+constexpr int kLTab = 2 * kLmaxMax + 1;         // Legendre table extent (l'' <= 2 l_max)
+constexpr int kRadStride = kLmaxMax + 1;        // F[type][t][l] stride
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Species data kept by the context.
+struct Species {
+  int lmax = 0, nl = 0, dpad = 0;  // N_L = (lmax+1)^2, depth block padded to 8 rows
+  double rmt = 0.0;
+  std::vector<double> u, du, udot, dudot, wr, un2, el;
+  std::vector<double> I[4];        // uu, uud, udu, udud
+  std::vector<double> T_override;  // empty or (2N_L)^2 complex (interleaved), col-major
+  double *d_T = nullptr;           // dpad x dpad complex col-major (ld = dpad)
+};
+
+// Per-species radial parameters read by the radial-factor kernel.
+struct RadialParams {
+  int lmax;
+  double rmt;
+  double u[kLmaxMax + 1], du[kLmaxMax + 1], udot[kLmaxMax + 1], dudot[kLmaxMax + 1];
+  double pre[kLmaxMax + 1];  // 4 pi / (W_l sqrt(Omega))
+};
+
+struct Workspace {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace hsg
+
+struct hsgen_ctx {
+  int device = 0;
+  hsgen_options opt{};
+  std::string err;
+  bool have_system = false;
+  double lattice[9]{};
+  double omega = 0.0;
+  std::vector<hsg::Species> types;
+  std::vector<int> toa;
+  std::vector<double> pos, rot;
+  std::vector<int> off;             // depth offset of each atom (n_atoms + 1)
+  int depth = 0;                    // total padded depth
+  std::vector<std::vector<int>> atoms_of_type;
+  // device copies of the system
+  int *d_toa = nullptr, *d_off = nullptr, *d_atoms_by_type = nullptr;
+  std::vector<int> atoms_by_type_start;  // start of each species' list in d_atoms_by_type
+  double *d_pos = nullptr, *d_rot = nullptr;
+  double *d_urow = nullptr;         // per depth row: 1 (A), ||u_dot_l||^2 (B), 0 (padding)
+  hsg::RadialParams *d_radial = nullptr;
+  // workspaces
+  hsg::Workspace ws_main;           // W, X, radial factors, kvec copy, split slices
+  hsg::Workspace ws_out;            // device H/S staging when the caller passes host pointers
+  // timing
+  cudaEvent_t ev[8]{};
+  bool events_ready = false;
+  hsgen_stats stats{};
+  int phase_used[8]{};
+};
+
+namespace hsg {
+
+// ---- error helpers ---------------------------------------------------------
+hsgen_status set_err(hsgen_ctx *ctx, hsgen_status st, const std::string &msg);
+hsgen_status cuda_err(hsgen_ctx *ctx, cudaError_t e, const char *what);
+#define HSG_CUDA(ctx, call)                                         \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return hsg::cuda_err((ctx), e_, #call);  \
+  } while (0)
+
+// ---- kernels (launch wrappers) ---------------------------------------------
+// a0/a1: per-species radial factors F[type][t][l] = pre_l * (f_A, f_B)(|K_t| r_MT).
+cudaError_t launch_radial(int n_g, const double *kvec, int n_types, const RadialParams *d_rp, double2 *F,
+                          cudaStream_t s);
+// a1: W[t][off_a + ...] = [A_a; B_a] for the atoms in `atoms` (one species).
+cudaError_t launch_coefficients(int lmax, int n_g, const double *kvec, const double2 *F_type, const int *atoms,
+                                int n_atoms, const double *pos, const double *rot, const int *off,
+                                int row_base, int dpad, double2 *W, long long ldw, cudaStream_t s);
+// a2: T matrix of one species (device, dpad x dpad complex, column-major).
+cudaError_t launch_tmatrix(const Species &sp, double2 *d_T, double *scratch, cudaStream_t s);
+// Recurrence tables in constant memory (called once per device).
+cudaError_t upload_tables();
+// a3: X_a = T_type W_a for all atoms of one species (FP64 DMMA).
+cudaError_t launch_tapply_fp64(int dpad, int n_g, const double2 *T, const int *atoms, int n_atoms,
+                               const int *off, int row_base, const double2 *W, double2 *X, long long ldw,
+                               cudaStream_t s);
+// a4: upper (or lower) triangle of H += W^H X and S += W^H diag(u) W (FP64 DMMA).
+cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *X, const double *urow,
+                           long long ldw, double2 *H, double2 *S, long long ld, int uplo, int accumulate,
+                           cudaStream_t s);
+// Mirror the written triangle into the other one (fill_full) and clear diagonal imaginary parts.
+cudaError_t launch_mirror(int n_g, double2 *M, long long ld, int uplo, cudaStream_t s);
+
+}  // namespace hsg
