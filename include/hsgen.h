@@ -101,6 +101,7 @@ typedef struct {
   int slices;              /* slices per operand used (split form)              */
   int n_kpoints;           /* k-points in the last call                         */
   long long workspace_bytes; /* device workspace currently held                 */
+  long long kernel_launches; /* kernels the last call launched                   */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -123,9 +124,11 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
  * K_t = k + G_t (host or device pointer). H and S are complex128 column-major
  * n_g x n_g with leading dimension ld >= n_g: device pointers (written
  * asynchronously on `cuda_stream`, a cudaStream_t or NULL for the default
- * stream) or host pointers (the library copies into them and the call
- * returns after the copy). Only the triangle named by opt.uplo is written
- * unless opt.fill_full; diagonal imaginary parts are set to 0. */
+ * stream; only the triangle named by opt.uplo is written unless
+ * opt.fill_full) or host pointers (computed in a library-owned device buffer
+ * and copied back in full, ld x n_g entries: the other triangle is zero
+ * unless opt.fill_full; the call returns after the copy). Diagonal imaginary
+ * parts are set to 0. */
 hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);
 

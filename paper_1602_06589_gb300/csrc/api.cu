@@ -368,7 +368,7 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
   auto chunks = atom_chunks(ctx);
   const bool single = chunks.size() == 1;
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
-  HSG_CUDA(ctx, launch_radial(n_g, job.kvec_dev, nt, ctx->d_radial, F, s));
+  HSG_LAUNCH(ctx, launch_radial(n_g, job.kvec_dev, nt, ctx->d_radial, F, s));
   int slices = split ? choose_slices(ctx->opt.target_rel_err, ctx->opt.slices) : 0;
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
     int a0 = chunks[ci].first, a1 = chunks[ci].second;
@@ -383,7 +383,7 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
       while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
       if (hi == lo) continue;
       const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
-      HSG_CUDA(ctx, launch_coefficients(ctx->types[t].lmax, n_g, job.kvec_dev, F + (size_t)t * n_g * kRadStride,
+      HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, n_g, job.kvec_dev, F + (size_t)t * n_g * kRadStride,
                                         d_atoms, hi - lo, ctx->d_pos, ctx->d_rot, ctx->d_off, row_base,
                                         ctx->types[t].dpad, W, L.ldw, s));
     }
@@ -402,7 +402,7 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
                                        L.ldw, ws + L.split, slices, s);
         if (st != HSGEN_OK) return st;
       } else {
-        HSG_CUDA(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].d_T, d_atoms,
+        HSG_LAUNCH(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].d_T, d_atoms,
                                          hi - lo, ctx->d_off, row_base, W, X, L.ldw, s));
       }
     }
@@ -414,14 +414,14 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
       if (st != HSGEN_OK) return st;
     } else {
       if (record && single) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
-      HSG_CUDA(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H, job.S, job.ld,
+      HSG_LAUNCH(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H, job.S, job.ld,
                                    ctx->opt.uplo, ci > 0 ? 1 : 0, s));
     }
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
   if (ctx->opt.fill_full) {
-    HSG_CUDA(ctx, launch_mirror(n_g, job.H, job.ld, ctx->opt.uplo, s));
-    HSG_CUDA(ctx, launch_mirror(n_g, job.S, job.ld, ctx->opt.uplo, s));
+    HSG_LAUNCH(ctx, launch_mirror(n_g, job.H, job.ld, ctx->opt.uplo, s));
+    HSG_LAUNCH(ctx, launch_mirror(n_g, job.S, job.ld, ctx->opt.uplo, s));
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
   ctx->stats.slices = slices;
@@ -477,11 +477,11 @@ hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, voi
     kd = (const double *)(ws + L.kvec);
   }
   double2 *F = (double2 *)(ws + L.F);
-  HSG_CUDA(ctx, launch_radial(n_g, kd, (int)ctx->types.size(), ctx->d_radial, F, s));
+  HSG_LAUNCH(ctx, launch_radial(n_g, kd, (int)ctx->types.size(), ctx->d_radial, F, s));
   for (int t = 0; t < (int)ctx->types.size(); ++t) {
     int n = (int)ctx->atoms_of_type[t].size();
     if (!n) continue;
-    HSG_CUDA(ctx, launch_coefficients(ctx->types[t].lmax, n_g, kd, F + (size_t)t * n_g * kRadStride,
+    HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, n_g, kd, F + (size_t)t * n_g * kRadStride,
                                       ctx->d_atoms_by_type + ctx->atoms_by_type_start[t], n, ctx->d_pos, ctx->d_rot,
                                       ctx->d_off, 0, ctx->types[t].dpad, (double2 *)W, ldw, s));
   }
@@ -530,10 +530,10 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
     if (st != HSGEN_OK) return st;
     job.H = (double2 *)ctx->ws_out.ptr;
     job.S = (double2 *)((char *)ctx->ws_out.ptr + hs_bytes);
-    // untouched triangle of a host output keeps its previous contents
-    HSG_CUDA(ctx, cudaMemcpyAsync(job.H, H, hs_bytes, cudaMemcpyHostToDevice, s));
-    HSG_CUDA(ctx, cudaMemcpyAsync(job.S, S, hs_bytes, cudaMemcpyHostToDevice, s));
+    // host outputs are written in full: the other triangle is zero unless fill_full
+    HSG_CUDA(ctx, cudaMemsetAsync(ctx->ws_out.ptr, 0, 2 * hs_bytes, s));
   }
+  ctx->launches = 0;
   st = run_kpoint(ctx, job, s, ws, L, true);
   if (st != HSGEN_OK) return st;
   if (!hdev) {
@@ -548,6 +548,7 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   ctx->stats.precision = ctx->opt.precision;
   ctx->stats.n_kpoints = 1;
   ctx->stats.flops_algorithmic = algorithmic_flops(ctx, n_g);
+  ctx->stats.kernel_launches = ctx->launches;
   ctx->phase_used[0] = atom_chunks(ctx).size() == 1;
   ctx->phase_used[1] = 1;
   return HSGEN_OK;
@@ -572,11 +573,14 @@ hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, con
     }
     return st;
   }
+  long long launches = 0;
   for (int k = 0; k < n_k; ++k) {
     st = hsgen_build_HS(ctx, n_g[k], kvec[k], H[k], S[k], ld[k], cuda_stream);
     if (st != HSGEN_OK) return st;
     flops += algorithmic_flops(ctx, n_g[k]);
+    launches += ctx->launches;
   }
+  ctx->stats.kernel_launches = launches;
   ctx->stats.flops_algorithmic = flops;
   ctx->stats.n_kpoints = n_k;
   ctx->phase_used[0] = 0;

@@ -68,6 +68,7 @@ struct hsgen_ctx {
   cudaEvent_t ev[8]{};
   bool events_ready = false;
   hsgen_stats stats{};
+  long long launches = 0;           // kernels launched by the current call
   int phase_used[8]{};
 };
 
@@ -80,6 +81,12 @@ hsgen_status cuda_err(hsgen_ctx *ctx, cudaError_t e, const char *what);
   do {                                                              \
     cudaError_t e_ = (call);                                        \
     if (e_ != cudaSuccess) return hsg::cuda_err((ctx), e_, #call);  \
+  } while (0)
+// A launch wrapper call that starts one kernel (counted for the stats).
+#define HSG_LAUNCH(ctx, call) \
+  do {                        \
+    HSG_CUDA(ctx, call);      \
+    ++(ctx)->launches;        \
   } while (0)
 
 // ---- kernels (launch wrappers) ---------------------------------------------

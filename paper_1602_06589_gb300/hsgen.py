@@ -44,7 +44,7 @@ class Stats(C.Structure):
     _fields_ = [("ms_coefficients", C.c_double), ("ms_tapply", C.c_double), ("ms_slice", C.c_double),
                 ("ms_contract", C.c_double), ("ms_total", C.c_double), ("flops_algorithmic", C.c_double),
                 ("precision", C.c_int), ("slices", C.c_int), ("n_kpoints", C.c_int),
-                ("workspace_bytes", C.c_longlong)]
+                ("workspace_bytes", C.c_longlong), ("kernel_launches", C.c_longlong)]
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
