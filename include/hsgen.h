@@ -144,6 +144,26 @@ hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, con
  * W + t*ldw, rows at the offsets hsgen_depth_layout reports, padding rows 0). */
 hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, void *W, long long ldw,
                                 void *cuda_stream);
+/* Same result as hsgen_coefficients, for callers that must not have the
+ * library allocate device memory (no counterpart in the paper). Code running
+ * under another framework's memory manager may find the GPU's memory already
+ * reserved, and latency-critical loops cannot accept the device
+ * synchronisation a cudaMalloc can cause; hsgen_coefficients may call
+ * cudaMalloc to grow its workspace, this function never does (nor cudaFree,
+ * nor any allocating routine). Its scratch (the radial factors) is a fixed
+ * 16 MiB array in device memory that belongs to the loaded library and is
+ * held on every GPU that loads it until the process exits; it limits
+ * n_types * n_g to 95325, larger requests return HSGEN_EINVAL without
+ * launching anything. kvec and W must be device pointers (HSGEN_EINVAL
+ * otherwise); the call is asynchronous on `cuda_stream`. The first call on a
+ * device looks up the array's device address (once per device); make that
+ * first call before capturing the stream into a graph. All calls, from every
+ * context, share the one array: calls whose kernels overlap on the GPU (on
+ * different streams, or from different host threads) race and must be
+ * ordered by the caller. Nothing needs clearing between calls: every entry
+ * read is written earlier in the same call. */
+hsgen_status hsgen_coefficients_noalloc(hsgen_ctx *ctx, int n_g, const double *kvec, void *W, long long ldw,
+                                        void *cuda_stream);
 /* T of species `type` (a2) copied into T (host, (2N_L)^2 complex, column-major). */
 hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T);
 /* Row offsets of the atoms in the depth of W (offsets[n_atoms+1], host); the

@@ -48,7 +48,7 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
-           "hsgen_coefficients", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_get_stats", "hsgen_last_error",
+           "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_get_stats", "hsgen_last_error",
            "hsgen_destroy"]
 
 _LIB = None
@@ -80,6 +80,7 @@ def load(path: Optional[str] = None):
         lib.hsgen_build_HS_batched.argtypes = [vp, C.c_int, _ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                                C.POINTER(C.c_longlong), vp]
         lib.hsgen_coefficients.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
+        lib.hsgen_coefficients_noalloc.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
         lib.hsgen_T_matrix.argtypes = [vp, C.c_int, _dp]
         lib.hsgen_depth_layout.argtypes = [vp, _ip, C.c_int]
         lib.hsgen_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -178,6 +179,14 @@ def hsgen_coefficients(ctx, n_g: int, kvec_ptr: int, W_ptr: int, ldw: int, strea
     st = load().hsgen_coefficients(ctx, int(n_g), C.c_void_p(kvec_ptr), C.c_void_p(W_ptr), int(ldw),
                                    C.c_void_p(stream))
     _check(ctx, st, "hsgen_coefficients")
+
+
+def hsgen_coefficients_noalloc(ctx, n_g: int, kvec_ptr: int, W_ptr: int, ldw: int, stream: int = 0):
+    """Like hsgen_coefficients but with no device allocation (fixed library scratch;
+    kvec and W on the device; n_types * n_g <= 95325)."""
+    st = load().hsgen_coefficients_noalloc(ctx, int(n_g), C.c_void_p(kvec_ptr), C.c_void_p(W_ptr), int(ldw),
+                                           C.c_void_p(stream))
+    _check(ctx, st, "hsgen_coefficients_noalloc")
 
 
 def hsgen_T_matrix(ctx, type_index: int, nl: int) -> np.ndarray:
