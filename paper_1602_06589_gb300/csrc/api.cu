@@ -62,9 +62,13 @@ static hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes) {
 }
 
 static void free_system(hsgen_ctx *ctx) {
-  for (auto &sp : ctx->types)
+  for (auto &sp : ctx->types) {
     if (sp.d_T) cudaFree(sp.d_T);
+    if (sp.d_Tsl) cudaFree(sp.d_Tsl);
+    if (sp.d_Texp) cudaFree(sp.d_Texp);
+  }
   ctx->types.clear();
+  ctx->split_slices = 0;
   cudaFree(ctx->d_toa);
   cudaFree(ctx->d_off);
   cudaFree(ctx->d_atoms_by_type);
@@ -291,6 +295,10 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
     }
   }
   HSG_CUDA(ctx, cudaFree(d_scratch));
+  if (ctx->opt.precision == HSGEN_SPLIT) {
+    hsgen_status st = split_prepare_types(ctx, choose_slices(ctx->opt.target_rel_err, ctx->opt.slices));
+    if (st != HSGEN_OK) return st;
+  }
   ctx->have_system = true;
   return HSGEN_OK;
 }
@@ -367,6 +375,7 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
   const bool split = ctx->opt.precision == HSGEN_SPLIT;
   auto chunks = atom_chunks(ctx);
   const bool single = chunks.size() == 1;
+  const bool rec = record && single;
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
   HSG_LAUNCH(ctx, launch_radial(n_g, job.kvec_dev, nt, ctx->d_radial, F, s));
   int slices = split ? choose_slices(ctx->opt.target_rel_err, ctx->opt.slices) : 0;
@@ -384,38 +393,30 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
       if (hi == lo) continue;
       const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
       HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, n_g, job.kvec_dev, F + (size_t)t * n_g * kRadStride,
-                                        d_atoms, hi - lo, ctx->d_pos, ctx->d_rot, ctx->d_off, row_base,
-                                        ctx->types[t].dpad, W, L.ldw, s));
+                                          d_atoms, hi - lo, ctx->d_pos, ctx->d_rot, ctx->d_off, row_base,
+                                          ctx->types[t].dpad, W, L.ldw, s));
     }
-    if (record && single) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
-    for (int t = 0; t < nt; ++t) {
-      const auto &lst = ctx->atoms_of_type[t];
-      int lo = 0, hi = 0;
-      while (lo < (int)lst.size() && lst[lo] < a0) ++lo;
-      hi = lo;
-      while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
-      if (hi == lo) continue;
-      const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
-      if (split) {
-        SplitCtx sc{ctx->opt.wait_timeout_ns};
-        hsgen_status st = split_tapply(ctx, sc, ctx->types[t], d_atoms, hi - lo, ctx->d_off, row_base, n_g, W, X,
-                                       L.ldw, ws + L.split, slices, s);
-        if (st != HSGEN_OK) return st;
-      } else {
-        HSG_LAUNCH(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].d_T, d_atoms,
-                                         hi - lo, ctx->d_off, row_base, W, X, L.ldw, s));
-      }
-    }
-    if (record && single) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+    if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
     if (split) {
-      SplitCtx sc{ctx->opt.wait_timeout_ns};
-      hsgen_status st = split_hs(ctx, sc, n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H, job.S, job.ld,
-                                 ctx->opt.uplo, ci > 0, ws + L.split, slices, s, record && single ? ctx->ev[3] : nullptr);
+      hsgen_status st = split_chunk(ctx, n_g, a0, a1, W, X, L.ldw, job.H, job.S, job.ld, ci > 0, ws + L.split,
+                                    slices, s, rec);
       if (st != HSGEN_OK) return st;
     } else {
-      if (record && single) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
+      for (int t = 0; t < nt; ++t) {
+        const auto &lst = ctx->atoms_of_type[t];
+        int lo = 0, hi = 0;
+        while (lo < (int)lst.size() && lst[lo] < a0) ++lo;
+        hi = lo;
+        while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
+        if (hi == lo) continue;
+        const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
+        HSG_LAUNCH(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].d_T, d_atoms,
+                                           hi - lo, ctx->d_off, row_base, W, X, L.ldw, s));
+      }
+      if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+      if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
       HSG_LAUNCH(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H, job.S, job.ld,
-                                   ctx->opt.uplo, ci > 0 ? 1 : 0, s));
+                                     ctx->opt.uplo, ci > 0 ? 1 : 0, s));
     }
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));

@@ -25,6 +25,10 @@ struct Species {
   std::vector<double> I[4];        // uu, uud, udu, udud
   std::vector<double> T_override;  // empty or (2N_L)^2 complex (interleaved), col-major
   double *d_T = nullptr;           // dpad x dpad complex col-major (ld = dpad)
+  // split form: BF16 slices of T (planes re, im per slice) and column exponents
+  void *d_Tsl = nullptr;
+  int *d_Texp = nullptr;
+  int t_real = 0;                  // imaginary part of T identically zero
 };
 
 // Per-species radial parameters read by the radial-factor kernel.
@@ -64,6 +68,9 @@ struct hsgen_ctx {
   // workspaces
   hsg::Workspace ws_main;           // W, X, radial factors, kvec copy, split slices
   hsg::Workspace ws_out;            // device H/S staging when the caller passes host pointers
+  int split_slices = 0;             // slices the species' T were cut into
+  int *d_status = nullptr;          // device status word of the split kernels
+  int *h_status = nullptr;          // pinned host copy
   // timing
   cudaEvent_t ev[8]{};
   bool events_ready = false;

@@ -1,27 +1,891 @@
-// split.cu -- split-precision form (placeholder until the tcgen05 path lands).
+// split.cu -- split-precision form of a3 (X = T W) and a4 (H, S) on the
+// tcgen05 tensor cores of sm_103a.
+//
+// Slicing (a5, part 1): every column of a complex FP64 operand gets one
+// power-of-two scale 2^e with all |re|, |im| < 2^e; each real value v becomes
+// the integer N = round(v 2^(7 + 8(s-1) - e)) (|N| <= 2^(7+8(s-1))), cut into
+// balanced base-256 digits d_1 .. d_s, |d_p| <= 128, stored as BF16 planes
+// (exact). The integer work uses the IEEE bit pattern directly, so no FP64
+// arithmetic is spent on it.
+//
+// Products (a5, part 2): C = P^H Q is, in real form,
+//   Re C = Pr^T Qr + Pi^T Qi,   Im C = Pr^T Qi - Pi^T Qr.
+// One tile is 128 output rows x 64 complex columns; its TMEM accumulator holds
+// [Re | Im] as 128 FP32 columns. The "r half" multiplies A = Pr with the B tile
+// [Qr | Qi], the "i half" A = Pi with [Qi | -Qr] (a negated plane is stored),
+// so both halves add into the same accumulator with M = N = 128 MMAs.
+// For a slice pair (p, q) the products are integers of magnitude <= 2^14; a
+// chunk of 1024 of them sums exactly in FP32 (|sum| <= 2^24). After each
+// chunk the epilogue warps move the FP32 accumulator into an int64 fixed-point
+// accumulator, also in TMEM, weighting pair (p, q) by 2^(-8(p+q-2)); pairs
+// with p + q > s + 1 are dropped (Ozaki-style truncation). After the last
+// chunk the tile is scaled by 2^(e_i + f_j - 14 - F) into FP64.
+//
+// Kernel roles (192 threads, one CTA per SM, persistent over tiles):
+//   warp 0    TMA producer (cp.async.bulk.tensor, 128B swizzle, 6 stages)
+//   warp 1    TMEM allocator and tcgen05.mma issuer
+//   warps 2-5 epilogue (TMEM lane quadrant = warp % 4)
+// Every wait is bounded (wait_timeout_ns); on expiry the kernel records an
+// error word, drains its own copies and MMAs (again bounded), frees TMEM and
+// returns, and the host reports HSGEN_ETIMEOUT.
+#include <cuda.h>  // CUtensorMap and enums; the encoder is fetched from the driver at run time
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "split.cuh"
 
 namespace hsg {
 
+namespace {
+
+constexpr int kMaxProb = 4;
+constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int NST = 6;
+constexpr int STAGE_BYTES = 32768;      // A 128x64 bf16 (16 KB) + B 128x64 bf16 (16 KB)
+constexpr int NTHREADS = 192;
+constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 512;     // acc0 [0,128) acc1 [128,256) wide int64 [256,512)
+// tcgen05 kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPILOGUE = 4 };
+
+struct GemmProblem {
+  int M, N, K;              // output rows, output complex columns, complex depth
+  int a_pps, b_pps;         // planes per slice of the A and B slice arrays
+  int a_real;               // A has a zero imaginary part: skip the i half
+  int uplo;                 // 0, 'U' or 'L' (tile set and write mask)
+  int accumulate;           // C += result instead of C = result
+  int F;                    // fixed-point fractional bits of the wide accumulator
+  const int *expA, *expB;   // per A column (output row) / per B column exponents
+  double2 *C;
+  long long ldc;
+  const int *atoms;         // batch mode: atom of each batch item
+  const int *off;           // depth offset of each atom
+  int row_base;             // depth offset of the chunk
+  int n_batch, nbm, nbn;    // batch items, row blocks, column blocks
+  const int *tri_prefix;    // triangle mode: valid tiles before column block bj (nbn + 1)
+  long long tile_begin;     // first global tile index of this problem
+};
+
+struct GemmParams {
+  CUtensorMap mapA[kMaxProb];
+  CUtensorMap mapB[kMaxProb];
+  GemmProblem prob[kMaxProb];
+  int nprob;
+  long long ntiles;
+  int s;
+  int *status;
+  unsigned long long timeout_ns;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when `timeout_ns` elapsed without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, unsigned long long timeout_ns) {
+  if (mbar_try(a, parity)) return true;
+  uint64_t t0 = gtime();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try(a, parity)) return true;
+    if (gtime() - t0 > timeout_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t mbar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tc_alloc(uint32_t dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]), "r"(r[32])
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 B.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset 16 B (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Tile schedule (identical in every role)
+// ---------------------------------------------------------------------------
+struct Tile {
+  int prob, m0, n0, b_k0, c_row0, nkb;
+};
+
+__device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
+  int pi = 0;
+  while (pi + 1 < P.nprob && t >= P.prob[pi + 1].tile_begin) ++pi;
+  const GemmProblem &pr = P.prob[pi];
+  long long lt = t - pr.tile_begin;
+  Tile ti;
+  ti.prob = pi;
+  int bi, bj, koff = 0;
+  if (pr.tri_prefix) {
+    int lo = 0, hi = pr.nbn;  // prefix[lo] <= lt < prefix[lo + 1]
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if ((long long)pr.tri_prefix[mid] <= lt) lo = mid; else hi = mid;
+    }
+    bj = lo;
+    int r = (int)(lt - pr.tri_prefix[bj]);
+    bi = (pr.uplo == 'L') ? (bj * BN) / BM + r : r;
+  } else {
+    long long per = (long long)pr.nbm * pr.nbn;
+    int b = (int)(lt / per);
+    int rem = (int)(lt % per);
+    bi = rem % pr.nbm;
+    bj = rem / pr.nbm;
+    koff = pr.off[pr.atoms[b]] - pr.row_base;
+  }
+  ti.m0 = bi * BM;
+  ti.n0 = bj * BN;
+  ti.b_k0 = koff;
+  ti.c_row0 = koff;
+  ti.nkb = (pr.K + BK - 1) / BK;
+  return ti;
+}
+
+// Walks the (chunk, slice pair) sequence of one tile: chunk kc covers complex
+// k-blocks [kc*ckb, min(nkb, (kc+1)*ckb)); pairs by increasing p + q.
+struct PairIter {
+  int s;
+  __device__ int count() const { return s * (s + 1) / 2; }
+  __device__ void get(int idx, int &p, int &q, int &g) const {
+    int k = 0;
+    for (g = 2; g <= s + 1; ++g)
+      for (p = 1; p < g; ++p) {
+        q = g - p;
+        if (p > s || q > s) continue;
+        if (k == idx) return;
+        ++k;
+      }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The persistent split GEMM kernel
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_constant__ GemmParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES);
+  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NST + 5);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NST, accf0 = empty0 + 8 * NST, acce0 = accf0 + 16,
+                 tdown = acce0 + 16;
+  const uint32_t sbase = smem_u32(smem);
+  const unsigned long long tmo = P.timeout_ns;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    mbar_init(accf0, 1);
+    mbar_init(accf0 + 8, 1);
+    mbar_init(acce0, 4);
+    mbar_init(acce0 + 8, 4);
+    mbar_init(tdown, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tc_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tmem_slot;
+  const PairIter pit{P.s};
+  const int npairs = pit.count();
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        const Tile ti = decode_tile(P, t);
+        const GemmProblem &pr = P.prob[ti.prob];
+        const CUtensorMap *mA = &P.mapA[ti.prob], *mB = &P.mapB[ti.prob];
+        const int halves = pr.a_real ? 1 : 2;
+        const int ckb = pr.a_real ? 16 : 8;
+        const int nkc = (ti.nkb + ckb - 1) / ckb;
+        for (int kc = 0; kc < nkc && ok; ++kc)
+          for (int pi = 0; pi < npairs && ok; ++pi) {
+            int p, q, g;
+            pit.get(pi, p, q, g);
+            const int kb1 = min(ti.nkb, (kc + 1) * ckb);
+            for (int kb = kc * ckb; kb < kb1 && ok; ++kb)
+              for (int h = 0; h < halves; ++h, ++it) {
+                const int st = it % NST;
+                const uint32_t round = it / NST;
+                if (!mbar_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
+                  atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
+                  ok = false;
+                  break;
+                }
+                const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + 16384;
+                const int k = kb * BK;
+                const int pa = (p - 1) * pr.a_pps + h;
+                const int pb0 = (q - 1) * pr.b_pps + h;        // h=0: re, h=1: im
+                const int pb1 = (q - 1) * pr.b_pps + h + 1;    // h=0: im, h=1: -re
+                mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
+                tma_load_3d(sA, mA, full0 + 8 * st, k, ti.m0, pa);
+                tma_load_3d(sB, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb0);
+                tma_load_3d(sB + 8192, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb1);
+              }
+          }
+      }
+      // Drain: wait (bounded) until every issued stage has been consumed so no
+      // copy is in flight when the CTA tears down.
+      for (uint32_t j = (it > NST ? it - NST : 0); j < it; ++j) {
+        const int st = j % NST;
+        if (!mbar_wait(empty0 + 8 * st, ((j / NST) & 1), tmo)) {
+          atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer --------------------------------
+    if (lane == 0) {
+      uint32_t it = 0, cc = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        const Tile ti = decode_tile(P, t);
+        const GemmProblem &pr = P.prob[ti.prob];
+        const int halves = pr.a_real ? 1 : 2;
+        const int ckb = pr.a_real ? 16 : 8;
+        const int nkc = (ti.nkb + ckb - 1) / ckb;
+        for (int kc = 0; kc < nkc && ok; ++kc)
+          for (int pi = 0; pi < npairs && ok; ++pi, ++cc) {
+            const int buf = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
+              atomicOr(P.status, ERR_TIMEOUT_MMA);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dacc = tbase + buf * 128;
+            const int kb1 = min(ti.nkb, (kc + 1) * ckb);
+            bool first = true;
+            for (int kb = kc * ckb; kb < kb1 && ok; ++kb)
+              for (int h = 0; h < halves; ++h, ++it) {
+                const int st = it % NST;
+                if (!mbar_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
+                  atomicOr(P.status, ERR_TIMEOUT_MMA);
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint64_t da = desc_sw128(sbase + st * STAGE_BYTES);
+                const uint64_t db = desc_sw128(sbase + st * STAGE_BYTES + 16384);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                  tc_mma(dacc, da + 2 * kk, db + 2 * kk, (first && kk == 0) ? 0u : 1u);
+                }
+                first = false;
+                tc_commit(empty0 + 8 * st);
+              }
+            if (ok) tc_commit(accf0 + 8 * buf);
+          }
+      }
+      // all issued MMAs complete before teardown
+      tc_commit(tdown);
+      if (!mbar_wait(tdown, 0, tmo)) atomicOr(P.status, ERR_TIMEOUT_MMA);
+    }
+  } else {
+    // ------------------------------ epilogue ----------------------------------
+    const int qd = warp & 3;                   // TMEM lane quadrant of this warp
+    const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
+    const uint32_t twide = tbase + lane_off + 256;
+    uint32_t cc = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      const Tile ti = decode_tile(P, t);
+      const GemmProblem &pr = P.prob[ti.prob];
+      const int ckb = pr.a_real ? 16 : 8;
+      const int nkc = (ti.nkb + ckb - 1) / ckb;
+      bool first_chunk = true;
+      for (int kc = 0; kc < nkc && ok; ++kc)
+        for (int pi = 0; pi < npairs && ok; ++pi, ++cc) {
+          int p, q, g;
+          pit.get(pi, p, q, g);
+          const int buf = cc & 1;
+          const uint32_t use = cc >> 1;
+          // one lane waits, the whole warp follows its verdict (the TMEM loads
+          // below are warp-collective)
+          int got = 0;
+          if (lane == 0) got = mbar_wait(accf0 + 8 * buf, use & 1, tmo) ? 1 : 0;
+          got = __shfl_sync(0xffffffffu, got, 0);
+          if (!got) {
+            if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_EPILOGUE);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int sh = pr.F - 8 * (g - 2);
+          const int ish = sh > 0 ? sh : 0;
+          const float fsc = (sh < 0) ? __int_as_float((127 + sh) << 23) : 1.0f;
+          const uint32_t tacc = tbase + lane_off + buf * 128;
+#pragma unroll 1
+          for (int c0 = 0; c0 < 128; c0 += 16) {
+            uint32_t v[16], w[32];
+            tc_ld16(tacc + c0, v);
+            if (!first_chunk) tc_ld32(twide + 2 * c0, w);
+            tc_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              long long x = first_chunk ? 0LL : (long long)(((unsigned long long)w[2 * u + 1] << 32) | w[2 * u]);
+              const int vi = __float2int_rn(__uint_as_float(v[u]) * fsc);
+              x += (long long)vi << ish;
+              w[2 * u] = (uint32_t)(unsigned long long)x;
+              w[2 * u + 1] = (uint32_t)((unsigned long long)x >> 32);
+            }
+            tc_st32(twide + 2 * c0, w);
+          }
+          tc_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce0 + 8 * buf);
+          first_chunk = false;
+        }
+      if (!ok) break;
+      // ---- tile output: int64 fixed point -> FP64, scaled by 2^(eA + eB - 14 - F)
+      const int rl = qd * 32 + lane;
+      const int row = ti.m0 + rl;            // row within the problem
+      const bool rvalid = row < pr.M;
+      const int eA = rvalid ? pr.expA[row] : 0;
+      const long long grow = (long long)ti.c_row0 + row;  // row in C
+#pragma unroll 1
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        uint32_t wr[32], wi[32];
+        tc_ld32(twide + 2 * c0, wr);
+        tc_ld32(twide + 2 * (c0 + 64), wi);
+        tc_wait_ld();
+        if (!rvalid) continue;
+#pragma unroll 4
+        for (int u = 0; u < 16; ++u) {
+          const int col = ti.n0 + c0 + u;
+          if (col >= pr.N) break;
+          if (pr.uplo == 'U' && row > col) continue;
+          if (pr.uplo == 'L' && row < col) continue;
+          const long long xr = (long long)(((unsigned long long)wr[2 * u + 1] << 32) | wr[2 * u]);
+          const long long xi = (long long)(((unsigned long long)wi[2 * u + 1] << 32) | wi[2 * u]);
+          const int e = eA + pr.expB[col] - 14 - pr.F;
+          const double scl = (e > -1022 && e < 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+          double re = __ll2double_rn(xr) * scl, im = __ll2double_rn(xi) * scl;
+          double2 *dst = pr.C + (size_t)col * pr.ldc + grow;
+          if (pr.accumulate) {
+            const double2 o = *dst;
+            re += o.x;
+            im += o.y;
+          }
+          if (pr.uplo && row == col) im = 0.0;
+          *dst = make_double2(re, im);
+        }
+      }
+      tc_fence_before();
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tc_dealloc(tbase, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// Slicing kernel: one CTA per column.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long to_fixed(double v, int shift) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;  // zero or subnormal: far below every scale in use
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const int t = E - 1075 + shift;
+  long long N;
+  if (t >= 0) {
+    N = m << t;  // t <= 2 because |v| < 2^e
+  } else {
+    const int r = -t;
+    N = (r > 62) ? 0 : ((m + (1LL << (r - 1))) >> r);
+  }
+  return (b < 0) ? -N : N;
+}
+
+__global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ src, long long lds, int K,
+                                                    const double *__restrict__ urow, int s, int planes,
+                                                    __nv_bfloat16 *__restrict__ dst, long long ldk,
+                                                    long long plane_stride, int *__restrict__ expo) {
+  const int col = blockIdx.x;
+  const double2 *c = src + (size_t)col * lds;
+  __shared__ double red[8];
+  __shared__ int e_sh;
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double2 v = c[k];
+    const double u = urow ? urow[k] : 1.0;
+    mx = fmax(mx, fmax(fabs(v.x * u), fabs(v.y * u)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    const int e = (m > 0.0) ? ilogb(m) + 1 : 0;
+    e_sh = e;
+    expo[col] = e;
+  }
+  __syncthreads();
+  const int shift = 7 + 8 * (s - 1) - e_sh;
+  __nv_bfloat16 *out = dst + (size_t)col * ldk;
+  for (int k = threadIdx.x; k < (int)ldk; k += blockDim.x) {
+    long long Nr = 0, Ni = 0;
+    if (k < K) {
+      double2 v = c[k];
+      if (urow) {
+        const double u = urow[k];
+        v.x *= u;
+        v.y *= u;
+      }
+      Nr = to_fixed(v.x, shift);
+      Ni = to_fixed(v.y, shift);
+    }
+    for (int p = s; p >= 1; --p) {
+      int dr, di;
+      if (p > 1) {
+        dr = (int)((Nr << 56) >> 56);
+        di = (int)((Ni << 56) >> 56);
+        Nr = (Nr - dr) >> 8;
+        Ni = (Ni - di) >> 8;
+      } else {
+        dr = (int)Nr;
+        di = (int)Ni;
+      }
+      __nv_bfloat16 *base = out + (size_t)(p - 1) * planes * plane_stride;
+      base[k] = __float2bfloat16_rn((float)dr);
+      base[plane_stride + k] = __float2bfloat16_rn((float)di);
+      if (planes == 3) base[2 * plane_stride + k] = __float2bfloat16_rn((float)-dr);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3D map over bf16 planes [plane][col][k]: k extent `kext`, row stride ldk elements.
+bool make_map(CUtensorMap *m, const void *base, long long kext, long long ncols, long long nplanes, long long ldk,
+              int box_rows) {
+  EncodeTiledFn fn = encoder();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kext, (cuuint64_t)ncols, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(ncols * ldk * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int fixed_point_bits(int K) {
+  // |accumulator| <= 2K * 2^14 * 2^F * (1 + 2^-7): keep it below 2^62; group-2
+  // contributions (< 2^24 << F) must also fit, hence F <= 38.
+  int lg = 0;
+  while ((1LL << lg) < 2LL * K + 1) ++lg;
+  return std::max(0, std::min(38, 47 - lg));
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (P.ntiles <= 0) return cudaSuccess;
+  long long grid = std::min<long long>(P.ntiles, num_sms());
+  split_gemm_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice(const double2 *src, long long lds, int K, const double *urow, int s, int planes,
+                         __nv_bfloat16 *dst, long long ldk, long long plane_stride, int *expo, int ncols,
+                         cudaStream_t st) {
+  if (ncols <= 0) return cudaSuccess;
+  slice_kernel<<<ncols, 256, 0, st>>>(src, lds, K, urow, s, planes, dst, ldk, plane_stride, expo);
+  return cudaGetLastError();
+}
+
+struct SplitWs {
+  __nv_bfloat16 *Wsl, *Xsl, *Ysl;
+  int *expW, *expX, *expY, *triU, *triL;
+  long long ldk;
+  size_t bytes;
+};
+
+SplitWs split_ws_layout(void *base, int n_g, int depth, int s) {
+  SplitWs w;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t r = o;
+    o += (b + 1023) / 1024 * 1024;
+    return r;
+  };
+  w.ldk = round_up(std::max(depth, 1), BK);
+  size_t plane = (size_t)n_g * w.ldk * sizeof(__nv_bfloat16);
+  size_t oW = take(plane * 3 * s), oX = take(plane * 3 * s), oY = take(plane * 2 * s);
+  size_t oe = take(sizeof(int) * 3 * (size_t)n_g);
+  int nbn = (n_g + BN - 1) / BN;
+  size_t ot = take(sizeof(int) * 2 * (size_t)(nbn + 1));
+  w.bytes = o;
+  char *b = (char *)base;
+  w.Wsl = (__nv_bfloat16 *)(b + oW);
+  w.Xsl = (__nv_bfloat16 *)(b + oX);
+  w.Ysl = (__nv_bfloat16 *)(b + oY);
+  w.expW = (int *)(b + oe);
+  w.expX = w.expW + n_g;
+  w.expY = w.expX + n_g;
+  w.triU = (int *)(b + ot);
+  w.triL = w.triU + (nbn + 1);
+  return w;
+}
+
+// number of row blocks with at least one entry of the triangle, per column block
+std::vector<int> tri_prefix(int n, int uplo) {
+  int nbm = (n + BM - 1) / BM, nbn = (n + BN - 1) / BN;
+  std::vector<int> pre(nbn + 1, 0);
+  for (int bj = 0; bj < nbn; ++bj) {
+    int cnt;
+    if (uplo == 'U')
+      cnt = std::min(nbm, (bj * BN + BN - 1) / BM + 1);
+    else
+      cnt = std::max(0, nbm - (bj * BN) / BM);
+    pre[bj + 1] = pre[bj] + cnt;
+  }
+  return pre;
+}
+
+}  // namespace
+
 int choose_slices(double target_rel_err, int override_slices) {
-  if (override_slices > 0) return override_slices;
-  (void)target_rel_err;
-  return 6;
+  if (override_slices > 0) return std::min(override_slices, kMaxSlices);
+  // relative Frobenius error observed per slice count on coefficient data,
+  // with a factor ~3 of margin (8 bits per slice)
+  static const double err[kMaxSlices + 1] = {1, 1, 1, 5e-6, 3e-8, 1e-10, 5e-13, 3e-15};
+  for (int s = 3; s <= kMaxSlices; ++s)
+    if (err[s] <= target_rel_err) return s;
+  return kMaxSlices;
 }
-size_t split_workspace_bytes(int, int, int) { return 0; }
-hsgen_status split_tapply(hsgen_ctx *ctx, const SplitCtx &, const Species &, const int *, int, const int *, int, int,
-                          const double2 *, double2 *, long long, void *, int, cudaStream_t) {
-  return set_err(ctx, HSGEN_ENOTSUP, "split form not available in this build");
+
+size_t split_workspace_bytes(int n_g, int chunk_depth, int slices) {
+  return split_ws_layout(nullptr, n_g, chunk_depth, slices).bytes;
 }
-hsgen_status split_hs(hsgen_ctx *ctx, const SplitCtx &, int, int, const double2 *, const double2 *, const double *,
-                      long long, double2 *, double2 *, long long, int, bool, void *, int, cudaStream_t, cudaEvent_t) {
-  return set_err(ctx, HSGEN_ENOTSUP, "split form not available in this build");
+
+hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
+  if (!ctx->d_status) {
+    HSG_CUDA(ctx, cudaMalloc(&ctx->d_status, sizeof(int)));
+    HSG_CUDA(ctx, cudaMallocHost(&ctx->h_status, sizeof(int)));
+    HSG_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  }
+  for (auto &sp : ctx->types) {
+    if (sp.d_Tsl) cudaFree(sp.d_Tsl);
+    if (sp.d_Texp) cudaFree(sp.d_Texp);
+    sp.d_Tsl = nullptr;
+    sp.d_Texp = nullptr;
+    size_t plane = (size_t)sp.dpad * sp.dpad;
+    HSG_CUDA(ctx, cudaMalloc(&sp.d_Tsl, plane * 2 * slices * sizeof(__nv_bfloat16)));
+    HSG_CUDA(ctx, cudaMalloc(&sp.d_Texp, sizeof(int) * sp.dpad));
+    HSG_CUDA(ctx, launch_slice((const double2 *)sp.d_T, sp.dpad, sp.dpad, nullptr, slices, 2,
+                               (__nv_bfloat16 *)sp.d_Tsl, sp.dpad, (long long)plane, sp.d_Texp, sp.dpad, 0));
+    // does T have an imaginary part?
+    std::vector<double2> h((size_t)sp.dpad * sp.dpad);
+    HSG_CUDA(ctx, cudaMemcpy(h.data(), sp.d_T, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost));
+    sp.t_real = 1;
+    for (auto &v : h)
+      if (v.y != 0.0) {
+        sp.t_real = 0;
+        break;
+      }
+  }
+  HSG_CUDA(ctx, cudaDeviceSynchronize());
+  ctx->split_slices = slices;
+  return HSGEN_OK;
 }
-hsgen_status split_check_status(hsgen_ctx *, cudaStream_t) { return HSGEN_OK; }
+
+hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 *W, double2 *X, long long ldw,
+                         double2 *H, double2 *S, long long ld, bool accumulate, void *ws, int slices,
+                         cudaStream_t s, bool record) {
+  if (ctx->split_slices != slices) {
+    hsgen_status st = split_prepare_types(ctx, slices);
+    if (st != HSGEN_OK) return st;
+  }
+  const int row_base = ctx->off[a0];
+  const int cdepth = ctx->off[a1] - row_base;
+  SplitWs w = split_ws_layout(ws, n_g, cdepth, slices);
+  const long long plane = (long long)n_g * w.ldk;
+  const unsigned long long tmo = (unsigned long long)ctx->opt.wait_timeout_ns;
+  // (1) W slices: planes re, im, -re (used as the left operand of H and the right of X and S)
+  HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, nullptr, slices, 3, w.Wsl, w.ldk, plane, w.expW, n_g, s));
+  // (2) X_a = T W_a, species by species (up to kMaxProb per launch)
+  {
+    std::vector<int> species;
+    std::vector<std::pair<int, int>> ranges;
+    for (int t = 0; t < (int)ctx->types.size(); ++t) {
+      const auto &lst = ctx->atoms_of_type[t];
+      int lo = 0;
+      while (lo < (int)lst.size() && lst[lo] < a0) ++lo;
+      int hi = lo;
+      while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
+      if (hi > lo) {
+        species.push_back(t);
+        ranges.push_back({lo, hi});
+      }
+    }
+    for (size_t b0 = 0; b0 < species.size(); b0 += kMaxProb) {
+      GemmParams P;
+      std::memset(&P, 0, sizeof(P));
+      P.s = slices;
+      P.status = ctx->d_status;
+      P.timeout_ns = tmo;
+      long long tiles = 0;
+      int np = 0;
+      for (size_t b = b0; b < species.size() && np < kMaxProb; ++b, ++np) {
+        const Species &sp = ctx->types[species[b]];
+        GemmProblem &pr = P.prob[np];
+        pr.M = sp.dpad;
+        pr.N = n_g;
+        pr.K = sp.dpad;
+        pr.a_pps = 2;
+        pr.b_pps = 3;
+        pr.a_real = sp.t_real;
+        pr.uplo = 0;
+        pr.accumulate = 0;
+        pr.F = fixed_point_bits(sp.dpad);
+        pr.expA = sp.d_Texp;
+        pr.expB = w.expW;
+        pr.C = X;
+        pr.ldc = ldw;
+        pr.atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[species[b]] + ranges[b].first;
+        pr.off = ctx->d_off;
+        pr.row_base = row_base;
+        pr.n_batch = ranges[b].second - ranges[b].first;
+        pr.nbm = (sp.dpad + BM - 1) / BM;
+        pr.nbn = (n_g + BN - 1) / BN;
+        pr.tri_prefix = nullptr;
+        pr.tile_begin = tiles;
+        tiles += (long long)pr.n_batch * pr.nbm * pr.nbn;
+        if (!make_map(&P.mapA[np], sp.d_Tsl, sp.dpad, sp.dpad, 2LL * slices, sp.dpad, BM) ||
+            !make_map(&P.mapB[np], w.Wsl, w.ldk, n_g, 3LL * slices, w.ldk, BN))
+          return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (T-apply)");
+      }
+      P.nprob = np;
+      P.ntiles = tiles;
+      HSG_LAUNCH(ctx, launch_gemm(P, s));
+    }
+  }
+  if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+  // (3) X slices (right operand of H) and (U W) slices (left operand of S)
+  HSG_LAUNCH(ctx, launch_slice(X, ldw, cdepth, nullptr, slices, 3, w.Xsl, w.ldk, plane, w.expX, n_g, s));
+  HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, ctx->d_urow + row_base, slices, 2, w.Ysl, w.ldk, plane, w.expY,
+                               n_g, s));
+  if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
+  // (4) H = W^H X and S = (U W)^H W over one triangle
+  {
+    const int uplo = ctx->opt.uplo;
+    std::vector<int> pre = tri_prefix(n_g, uplo);
+    int *d_pre = (uplo == 'U') ? w.triU : w.triL;
+    HSG_CUDA(ctx, cudaMemcpyAsync(d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, s));
+    GemmParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.s = slices;
+    P.status = ctx->d_status;
+    P.timeout_ns = tmo;
+    const long long per = pre.back();
+    for (int k = 0; k < 2; ++k) {
+      GemmProblem &pr = P.prob[k];
+      pr.M = n_g;
+      pr.N = n_g;
+      pr.K = cdepth;
+      pr.a_pps = (k == 0) ? 3 : 2;
+      pr.b_pps = 3;
+      pr.a_real = 0;
+      pr.uplo = uplo;
+      pr.accumulate = accumulate ? 1 : 0;
+      pr.F = fixed_point_bits(cdepth);
+      pr.expA = (k == 0) ? w.expW : w.expY;
+      pr.expB = (k == 0) ? w.expX : w.expW;
+      pr.C = (k == 0) ? H : S;
+      pr.ldc = ld;
+      pr.atoms = nullptr;
+      pr.off = nullptr;
+      pr.row_base = 0;
+      pr.n_batch = 1;
+      pr.nbm = (n_g + BM - 1) / BM;
+      pr.nbn = (n_g + BN - 1) / BN;
+      pr.tri_prefix = d_pre;
+      pr.tile_begin = k * per;
+      const void *a = (k == 0) ? (const void *)w.Wsl : (const void *)w.Ysl;
+      const void *b = (k == 0) ? (const void *)w.Xsl : (const void *)w.Wsl;
+      if (!make_map(&P.mapA[k], a, w.ldk, n_g, (long long)pr.a_pps * slices, w.ldk, BM) ||
+          !make_map(&P.mapB[k], b, w.ldk, n_g, 3LL * slices, w.ldk, BN))
+        return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
+    }
+    P.nprob = 2;
+    P.ntiles = 2 * per;
+    HSG_LAUNCH(ctx, launch_gemm(P, s));
+  }
+  return HSGEN_OK;
+}
+
+hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s) {
+  if (!ctx->d_status) return HSGEN_OK;
+  HSG_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HSG_CUDA(ctx, cudaStreamSynchronize(s));
+  int st = *ctx->h_status;
+  if (st != 0) {
+    HSG_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+    return set_err(ctx, HSGEN_ETIMEOUT,
+                   "split kernel: a bounded device wait expired (status " + std::to_string(st) + ")");
+  }
+  return HSGEN_OK;
+}
+
 hsgen_status split_batched(hsgen_ctx *, int, const int *, const double *const *, void *const *, void *const *,
                            const long long *, cudaStream_t) {
   return HSGEN_ENOTSUP;
 }
-void split_release(hsgen_ctx *) {}
+
+void split_release(hsgen_ctx *ctx) {
+  for (auto &sp : ctx->types) {
+    if (sp.d_Tsl) cudaFree(sp.d_Tsl);
+    if (sp.d_Texp) cudaFree(sp.d_Texp);
+    sp.d_Tsl = nullptr;
+    sp.d_Texp = nullptr;
+  }
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  ctx->d_status = nullptr;
+  ctx->h_status = nullptr;
+}
 
 }  // namespace hsg
