@@ -71,6 +71,9 @@ struct hsgen_ctx {
   int split_slices = 0;             // slices the species' T were cut into
   int *d_status = nullptr;          // device status word of the split kernels
   int *h_status = nullptr;          // pinned host copy
+  void *d_tiles = nullptr;          // split form: tile list of one triangle (int2 row/column blocks)
+  int tiles_n = -1, tiles_uplo = 0;
+  long long tiles_count = 0;
   // timing
   cudaEvent_t ev[8]{};
   bool events_ready = false;

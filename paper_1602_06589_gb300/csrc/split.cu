@@ -68,7 +68,7 @@ struct GemmProblem {
   const int *off;           // depth offset of each atom
   int row_base;             // depth offset of the chunk
   int n_batch, nbm, nbn;    // batch items, row blocks, column blocks
-  const int *tri_prefix;    // triangle mode: valid tiles before column block bj (nbn + 1)
+  const int2 *tile_list;    // triangle mode: (row block, column block) of every tile, L2-friendly order
   long long tile_begin;     // first global tile index of this problem
 };
 
@@ -205,15 +205,10 @@ __device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
   Tile ti;
   ti.prob = pi;
   int bi, bj, koff = 0;
-  if (pr.tri_prefix) {
-    int lo = 0, hi = pr.nbn;  // prefix[lo] <= lt < prefix[lo + 1]
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if ((long long)pr.tri_prefix[mid] <= lt) lo = mid; else hi = mid;
-    }
-    bj = lo;
-    int r = (int)(lt - pr.tri_prefix[bj]);
-    bi = (pr.uplo == 'L') ? (bj * BN) / BM + r : r;
+  if (pr.tile_list) {
+    const int2 bij = pr.tile_list[lt];
+    bi = bij.x;
+    bj = bij.y;
   } else {
     long long per = (long long)pr.nbm * pr.nbn;
     int b = (int)(lt / per);
@@ -230,20 +225,20 @@ __device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
   return ti;
 }
 
-// Walks the (chunk, slice pair) sequence of one tile: chunk kc covers complex
-// k-blocks [kc*ckb, min(nkb, (kc+1)*ckb)); pairs by increasing p + q.
-struct PairIter {
-  int s;
-  __device__ int count() const { return s * (s + 1) / 2; }
-  __device__ void get(int idx, int &p, int &q, int &g) const {
-    int k = 0;
-    for (g = 2; g <= s + 1; ++g)
-      for (p = 1; p < g; ++p) {
-        q = g - p;
-        if (p > s || q > s) continue;
-        if (k == idx) return;
-        ++k;
-      }
+// The accumulation schedule of one tile, identical in every role: chunk kc
+// covers complex k-blocks [kc*ckb, min(nkb, (kc+1)*ckb)); within it, slice
+// pairs (p, g-p) go by increasing weight class g = p + q <= s + 1, and up to
+// `ppc` pairs of one class share a chunk when their products still fit the
+// 1024-product exactness bound (short depths, e.g. X = T W).
+struct Sched {
+  int s, nkb, ckb, nkc, halves, ppc;
+  __device__ Sched(const GemmProblem &pr, const Tile &ti, int s_) : s(s_) {
+    nkb = ti.nkb;
+    halves = pr.a_real ? 1 : 2;
+    ckb = pr.a_real ? 16 : 8;
+    nkc = (nkb + ckb - 1) / ckb;
+    const int per_pair = (nkb < ckb ? nkb : ckb) * BK * halves;  // products per output and pair
+    ppc = (nkc == 1) ? max(1, 1024 / per_pair) : 1;
   }
 };
 
@@ -282,8 +277,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const PairIter pit{P.s};
-  const int npairs = pit.count();
+  const int S = P.s;
+  // teardown waits: long enough for copies and MMAs already issued to finish
+  const unsigned long long drain = tmo > 1000000000ull ? tmo : 1000000000ull;
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
@@ -293,44 +289,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
       for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
         const Tile ti = decode_tile(P, t);
         const GemmProblem &pr = P.prob[ti.prob];
+        const Sched sc(pr, ti, S);
         const CUtensorMap *mA = &P.mapA[ti.prob], *mB = &P.mapB[ti.prob];
-        const int halves = pr.a_real ? 1 : 2;
-        const int ckb = pr.a_real ? 16 : 8;
-        const int nkc = (ti.nkb + ckb - 1) / ckb;
-        for (int kc = 0; kc < nkc && ok; ++kc)
-          for (int pi = 0; pi < npairs && ok; ++pi) {
-            int p, q, g;
-            pit.get(pi, p, q, g);
-            const int kb1 = min(ti.nkb, (kc + 1) * ckb);
-            for (int kb = kc * ckb; kb < kb1 && ok; ++kb)
-              for (int h = 0; h < halves; ++h, ++it) {
-                const int st = it % NST;
-                const uint32_t round = it / NST;
-                if (!mbar_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
-                  atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
-                  ok = false;
-                  break;
-                }
-                const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + 16384;
-                const int k = kb * BK;
-                const int pa = (p - 1) * pr.a_pps + h;
-                const int pb0 = (q - 1) * pr.b_pps + h;        // h=0: re, h=1: im
-                const int pb1 = (q - 1) * pr.b_pps + h + 1;    // h=0: im, h=1: -re
-                mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
-                tma_load_3d(sA, mA, full0 + 8 * st, k, ti.m0, pa);
-                tma_load_3d(sB, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb0);
-                tma_load_3d(sB + 8192, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb1);
+        for (int kc = 0; kc < sc.nkc && ok; ++kc) {
+          const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
+          for (int g = 2; g <= S + 1 && ok; ++g) {
+            const int plo = max(1, g - S), phi = min(S, g - 1);
+            for (int pb = plo; pb <= phi && ok; pb += sc.ppc) {
+              const int pe = min(phi, pb + sc.ppc - 1);
+              for (int p = pb; p <= pe && ok; ++p) {
+                const int q = g - p;
+                for (int kb = kb0; kb < kb1 && ok; ++kb)
+                  for (int h = 0; h < sc.halves; ++h, ++it) {
+                    const int st = it % NST;
+                    const uint32_t round = it / NST;
+                    if (!mbar_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
+                      atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
+                      ok = false;
+                      break;
+                    }
+                    const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + 16384;
+                    const int k = kb * BK;
+                    const int pa = (p - 1) * pr.a_pps + h;
+                    const int pb0 = (q - 1) * pr.b_pps + h;      // h=0: re, h=1: im
+                    const int pb1 = (q - 1) * pr.b_pps + h + 1;  // h=0: im, h=1: -re
+                    mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
+                    tma_load_3d(sA, mA, full0 + 8 * st, k, ti.m0, pa);
+                    tma_load_3d(sB, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb0);
+                    tma_load_3d(sB + 8192, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb1);
+                  }
               }
+            }
           }
-      }
-      // Drain: wait (bounded) until every issued stage has been consumed so no
-      // copy is in flight when the CTA tears down.
-      for (uint32_t j = (it > NST ? it - NST : 0); j < it; ++j) {
-        const int st = j % NST;
-        if (!mbar_wait(empty0 + 8 * st, ((j / NST) & 1), tmo)) {
-          atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
-          break;
         }
+      }
+      // no copy may still be in flight at teardown: the latest use of every
+      // stage must have landed (bounded)
+      for (int st = 0; st < NST; ++st) {
+        if (it <= (uint32_t)st) break;
+        const uint32_t j = st + NST * ((it - 1 - st) / NST);
+        if (!mbar_wait(full0 + 8 * st, (j / NST) & 1, drain)) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
       }
     }
   } else if (warp == 1) {
@@ -341,50 +339,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
       for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
         const Tile ti = decode_tile(P, t);
         const GemmProblem &pr = P.prob[ti.prob];
-        const int halves = pr.a_real ? 1 : 2;
-        const int ckb = pr.a_real ? 16 : 8;
-        const int nkc = (ti.nkb + ckb - 1) / ckb;
-        for (int kc = 0; kc < nkc && ok; ++kc)
-          for (int pi = 0; pi < npairs && ok; ++pi, ++cc) {
-            const int buf = cc & 1;
-            const uint32_t use = cc >> 1;
-            if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
-              atomicOr(P.status, ERR_TIMEOUT_MMA);
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t dacc = tbase + buf * 128;
-            const int kb1 = min(ti.nkb, (kc + 1) * ckb);
-            bool first = true;
-            for (int kb = kc * ckb; kb < kb1 && ok; ++kb)
-              for (int h = 0; h < halves; ++h, ++it) {
-                const int st = it % NST;
-                if (!mbar_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
-                  atomicOr(P.status, ERR_TIMEOUT_MMA);
-                  ok = false;
-                  break;
-                }
-                tc_fence_after();
-                const uint64_t da = desc_sw128(sbase + st * STAGE_BYTES);
-                const uint64_t db = desc_sw128(sbase + st * STAGE_BYTES + 16384);
-#pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                  tc_mma(dacc, da + 2 * kk, db + 2 * kk, (first && kk == 0) ? 0u : 1u);
-                }
-                first = false;
-                tc_commit(empty0 + 8 * st);
+        const Sched sc(pr, ti, S);
+        for (int kc = 0; kc < sc.nkc && ok; ++kc) {
+          const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
+          for (int g = 2; g <= S + 1 && ok; ++g) {
+            const int plo = max(1, g - S), phi = min(S, g - 1);
+            for (int pb = plo; pb <= phi && ok; pb += sc.ppc, ++cc) {
+              const int pe = min(phi, pb + sc.ppc - 1);
+              const int buf = cc & 1;
+              const uint32_t use = cc >> 1;
+              if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
+                atomicOr(P.status, ERR_TIMEOUT_MMA);
+                ok = false;
+                break;
               }
-            if (ok) tc_commit(accf0 + 8 * buf);
+              tc_fence_after();
+              const uint32_t dacc = tbase + buf * 128;
+              bool first = true;
+              for (int p = pb; p <= pe && ok; ++p)
+                for (int kb = kb0; kb < kb1 && ok; ++kb)
+                  for (int h = 0; h < sc.halves; ++h, ++it) {
+                    const int st = it % NST;
+                    if (!mbar_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
+                      atomicOr(P.status, ERR_TIMEOUT_MMA);
+                      ok = false;
+                      break;
+                    }
+                    tc_fence_after();
+                    const uint64_t da = desc_sw128(sbase + st * STAGE_BYTES);
+                    const uint64_t db = desc_sw128(sbase + st * STAGE_BYTES + 16384);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) tc_mma(dacc, da + 2 * kk, db + 2 * kk, (first && kk == 0) ? 0u : 1u);
+                    first = false;
+                    tc_commit(empty0 + 8 * st);
+                  }
+              if (ok) tc_commit(accf0 + 8 * buf);
+            }
           }
+        }
       }
-      // all issued MMAs complete before teardown
+      // every MMA issued has completed before TMEM is released (bounded)
       tc_commit(tdown);
-      if (!mbar_wait(tdown, 0, tmo)) atomicOr(P.status, ERR_TIMEOUT_MMA);
+      if (!mbar_wait(tdown, 0, drain)) atomicOr(P.status, ERR_TIMEOUT_MMA);
     }
   } else {
     // ------------------------------ epilogue ----------------------------------
-    const int qd = warp & 3;                   // TMEM lane quadrant of this warp
+    const int qd = warp & 3;  // TMEM lane quadrant of this warp
     const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
     const uint32_t twide = tbase + lane_off + 256;
     uint32_t cc = 0;
@@ -392,56 +392,56 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const Tile ti = decode_tile(P, t);
       const GemmProblem &pr = P.prob[ti.prob];
-      const int ckb = pr.a_real ? 16 : 8;
-      const int nkc = (ti.nkb + ckb - 1) / ckb;
+      const Sched sc(pr, ti, S);
       bool first_chunk = true;
-      for (int kc = 0; kc < nkc && ok; ++kc)
-        for (int pi = 0; pi < npairs && ok; ++pi, ++cc) {
-          int p, q, g;
-          pit.get(pi, p, q, g);
-          const int buf = cc & 1;
-          const uint32_t use = cc >> 1;
-          // one lane waits, the whole warp follows its verdict (the TMEM loads
-          // below are warp-collective)
-          int got = 0;
-          if (lane == 0) got = mbar_wait(accf0 + 8 * buf, use & 1, tmo) ? 1 : 0;
-          got = __shfl_sync(0xffffffffu, got, 0);
-          if (!got) {
-            if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_EPILOGUE);
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const int sh = pr.F - 8 * (g - 2);
-          const int ish = sh > 0 ? sh : 0;
-          const float fsc = (sh < 0) ? __int_as_float((127 + sh) << 23) : 1.0f;
-          const uint32_t tacc = tbase + lane_off + buf * 128;
-#pragma unroll 1
-          for (int c0 = 0; c0 < 128; c0 += 16) {
-            uint32_t v[16], w[32];
-            tc_ld16(tacc + c0, v);
-            if (!first_chunk) tc_ld32(twide + 2 * c0, w);
-            tc_wait_ld();
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              long long x = first_chunk ? 0LL : (long long)(((unsigned long long)w[2 * u + 1] << 32) | w[2 * u]);
-              const int vi = __float2int_rn(__uint_as_float(v[u]) * fsc);
-              x += (long long)vi << ish;
-              w[2 * u] = (uint32_t)(unsigned long long)x;
-              w[2 * u + 1] = (uint32_t)((unsigned long long)x >> 32);
+      for (int kc = 0; kc < sc.nkc && ok; ++kc)
+        for (int g = 2; g <= S + 1 && ok; ++g) {
+          const int plo = max(1, g - S), phi = min(S, g - 1);
+          for (int pb = plo; pb <= phi && ok; pb += sc.ppc, ++cc) {
+            const int buf = cc & 1;
+            const uint32_t use = cc >> 1;
+            // one lane waits, the whole warp follows its verdict (the TMEM loads
+            // below are warp-collective)
+            int got = 0;
+            if (lane == 0) got = mbar_wait(accf0 + 8 * buf, use & 1, tmo) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+              if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_EPILOGUE);
+              ok = false;
+              break;
             }
-            tc_st32(twide + 2 * c0, w);
+            tc_fence_after();
+            const int sh = pr.F - 8 * (g - 2);
+            const int ish = sh > 0 ? sh : 0;
+            const float fsc = (sh < 0) ? __int_as_float((127 + sh) << 23) : 1.0f;
+            const uint32_t tacc = tbase + lane_off + buf * 128;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 128; c0 += 16) {
+              uint32_t v[16], w[32];
+              tc_ld16(tacc + c0, v);
+              if (!first_chunk) tc_ld32(twide + 2 * c0, w);
+              tc_wait_ld();
+#pragma unroll
+              for (int u = 0; u < 16; ++u) {
+                long long x = first_chunk ? 0LL : (long long)(((unsigned long long)w[2 * u + 1] << 32) | w[2 * u]);
+                const int vi = __float2int_rn(__uint_as_float(v[u]) * fsc);
+                x += (long long)vi << ish;
+                w[2 * u] = (uint32_t)(unsigned long long)x;
+                w[2 * u + 1] = (uint32_t)((unsigned long long)x >> 32);
+              }
+              tc_st32(twide + 2 * c0, w);
+            }
+            tc_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * buf);
+            first_chunk = false;
           }
-          tc_wait_st();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(acce0 + 8 * buf);
-          first_chunk = false;
         }
       if (!ok) break;
       // ---- tile output: int64 fixed point -> FP64, scaled by 2^(eA + eB - 14 - F)
       const int rl = qd * 32 + lane;
-      const int row = ti.m0 + rl;            // row within the problem
+      const int row = ti.m0 + rl;  // row within the problem
       const bool rvalid = row < pr.M;
       const int eA = rvalid ? pr.expA[row] : 0;
       const long long grow = (long long)ti.c_row0 + row;  // row in C
@@ -452,16 +452,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
         tc_ld32(twide + 2 * (c0 + 64), wi);
         tc_wait_ld();
         if (!rvalid) continue;
-#pragma unroll 4
+#pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int col = ti.n0 + c0 + u;
-          if (col >= pr.N) break;
-          if (pr.uplo == 'U' && row > col) continue;
-          if (pr.uplo == 'L' && row < col) continue;
+          const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
+          if (!keep) continue;
           const long long xr = (long long)(((unsigned long long)wr[2 * u + 1] << 32) | wr[2 * u]);
           const long long xi = (long long)(((unsigned long long)wi[2 * u + 1] << 32) | wi[2 * u]);
           const int e = eA + pr.expB[col] - 14 - pr.F;
-          const double scl = (e > -1022 && e < 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+          const double scl =
+              (e > -1022 && e < 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
           double re = __ll2double_rn(xr) * scl, im = __ll2double_rn(xi) * scl;
           double2 *dst = pr.C + (size_t)col * pr.ldc + grow;
           if (pr.accumulate) {
@@ -638,7 +638,7 @@ cudaError_t launch_slice(const double2 *src, long long lds, int K, const double 
 
 struct SplitWs {
   __nv_bfloat16 *Wsl, *Xsl, *Ysl;
-  int *expW, *expX, *expY, *triU, *triL;
+  int *expW, *expX, *expY;
   long long ldk;
   size_t bytes;
 };
@@ -655,8 +655,6 @@ SplitWs split_ws_layout(void *base, int n_g, int depth, int s) {
   size_t plane = (size_t)n_g * w.ldk * sizeof(__nv_bfloat16);
   size_t oW = take(plane * 3 * s), oX = take(plane * 3 * s), oY = take(plane * 2 * s);
   size_t oe = take(sizeof(int) * 3 * (size_t)n_g);
-  int nbn = (n_g + BN - 1) / BN;
-  size_t ot = take(sizeof(int) * 2 * (size_t)(nbn + 1));
   w.bytes = o;
   char *b = (char *)base;
   w.Wsl = (__nv_bfloat16 *)(b + oW);
@@ -665,24 +663,25 @@ SplitWs split_ws_layout(void *base, int n_g, int depth, int s) {
   w.expW = (int *)(b + oe);
   w.expX = w.expW + n_g;
   w.expY = w.expX + n_g;
-  w.triU = (int *)(b + ot);
-  w.triL = w.triU + (nbn + 1);
   return w;
 }
 
-// number of row blocks with at least one entry of the triangle, per column block
-std::vector<int> tri_prefix(int n, int uplo) {
-  int nbm = (n + BM - 1) / BM, nbn = (n + BN - 1) / BN;
-  std::vector<int> pre(nbn + 1, 0);
-  for (int bj = 0; bj < nbn; ++bj) {
-    int cnt;
-    if (uplo == 'U')
-      cnt = std::min(nbm, (bj * BN + BN - 1) / BM + 1);
-    else
-      cnt = std::max(0, nbm - (bj * BN) / BM);
-    pre[bj + 1] = pre[bj] + cnt;
+// Tiles of one triangle, in bands of kBand column blocks: within a band all
+// row blocks in order, so the ~one wave of tiles that runs at a time shares a
+// few A row blocks and kBand B column blocks through L2.
+std::vector<int2> tri_tiles(int n, int uplo) {
+  constexpr int kBand = 16;
+  const int nbm = (n + BM - 1) / BM, nbn = (n + BN - 1) / BN;
+  std::vector<int2> out;
+  for (int b0 = 0; b0 < nbn; b0 += kBand) {
+    const int b1 = std::min(nbn, b0 + kBand);
+    for (int bi = 0; bi < nbm; ++bi)
+      for (int bj = b0; bj < b1; ++bj) {
+        const bool valid = (uplo == 'U') ? (bi * BM <= bj * BN + BN - 1) : (bi * BM + BM - 1 >= bj * BN);
+        if (valid) out.push_back(make_int2(bi, bj));
+      }
   }
-  return pre;
+  return out;
 }
 
 }  // namespace
@@ -791,7 +790,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
         pr.n_batch = ranges[b].second - ranges[b].first;
         pr.nbm = (sp.dpad + BM - 1) / BM;
         pr.nbn = (n_g + BN - 1) / BN;
-        pr.tri_prefix = nullptr;
+        pr.tile_list = nullptr;
         pr.tile_begin = tiles;
         tiles += (long long)pr.n_batch * pr.nbm * pr.nbn;
         if (!make_map(&P.mapA[np], sp.d_Tsl, sp.dpad, sp.dpad, 2LL * slices, sp.dpad, BM) ||
@@ -812,15 +811,23 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
   // (4) H = W^H X and S = (U W)^H W over one triangle
   {
     const int uplo = ctx->opt.uplo;
-    std::vector<int> pre = tri_prefix(n_g, uplo);
-    int *d_pre = (uplo == 'U') ? w.triU : w.triL;
-    HSG_CUDA(ctx, cudaMemcpyAsync(d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, s));
+    if (ctx->tiles_n != n_g || ctx->tiles_uplo != uplo) {
+      std::vector<int2> tl = tri_tiles(n_g, uplo);
+      if (ctx->d_tiles) cudaFree(ctx->d_tiles);
+      ctx->d_tiles = nullptr;
+      ctx->tiles_n = -1;
+      HSG_CUDA(ctx, cudaMalloc(&ctx->d_tiles, sizeof(int2) * std::max<size_t>(tl.size(), 1)));
+      HSG_CUDA(ctx, cudaMemcpy(ctx->d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
+      ctx->tiles_n = n_g;
+      ctx->tiles_uplo = uplo;
+      ctx->tiles_count = (long long)tl.size();
+    }
     GemmParams P;
     std::memset(&P, 0, sizeof(P));
     P.s = slices;
     P.status = ctx->d_status;
     P.timeout_ns = tmo;
-    const long long per = pre.back();
+    const long long per = ctx->tiles_count;
     for (int k = 0; k < 2; ++k) {
       GemmProblem &pr = P.prob[k];
       pr.M = n_g;
@@ -842,7 +849,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       pr.n_batch = 1;
       pr.nbm = (n_g + BM - 1) / BM;
       pr.nbn = (n_g + BN - 1) / BN;
-      pr.tri_prefix = d_pre;
+      pr.tile_list = (const int2 *)ctx->d_tiles;
       pr.tile_begin = k * per;
       const void *a = (k == 0) ? (const void *)w.Wsl : (const void *)w.Ysl;
       const void *b = (k == 0) ? (const void *)w.Xsl : (const void *)w.Wsl;
@@ -882,6 +889,9 @@ void split_release(hsgen_ctx *ctx) {
     sp.d_Tsl = nullptr;
     sp.d_Texp = nullptr;
   }
+  if (ctx->d_tiles) cudaFree(ctx->d_tiles);
+  ctx->d_tiles = nullptr;
+  ctx->tiles_n = -1;
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   ctx->d_status = nullptr;
