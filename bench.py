@@ -167,13 +167,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-columns", type=int, default=24)
+    ap.add_argument("--n-g", type=int, default=0, help="override N_G (smaller cases for profiling)")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="also time one FP64-form step on the same workload")
     args = ap.parse_args()
 
     from workloads import make_config
 
-    w = make_config(args.config)
+    w = make_config(args.config, n_g_override=args.n_g or None)
     if args.impl == "reference":
         run_reference(args, w)
         return

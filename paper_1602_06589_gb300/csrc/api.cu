@@ -8,6 +8,7 @@
 //   a6    steps a1-a5 repeated per chunk of atoms, accumulating into H, S
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -133,6 +134,7 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   if (!ctx) return HSGEN_ENOMEM;
   ctx->device = cuda_device;
   ctx->opt = o;
+  if (const char *ks = std::getenv("HSGEN_KSEG_BLOCKS")) ctx->kseg_blocks = std::max(1, std::atoi(ks));
   if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess) {
     delete ctx;
     return HSGEN_ECUDA;
@@ -173,7 +175,9 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
     int n1 = ty.lmax + 1;
     sp.lmax = ty.lmax;
     sp.nl = n1 * n1;
-    sp.dpad = round_up(2 * sp.nl, 8);
+    // depth block of one atom: 8-row aligned (16-byte TMA rule), 64-row aligned
+    // in the split form so that every k-block of the BF16 slices is whole
+    sp.dpad = round_up(2 * sp.nl, ctx->opt.precision == HSGEN_SPLIT ? 64 : 8);
     sp.rmt = ty.rmt;
     sp.u.assign(ty.u, ty.u + n1);
     sp.du.assign(ty.du, ty.du + n1);

@@ -74,6 +74,7 @@ struct hsgen_ctx {
   void *d_tiles = nullptr;          // split form: tile list of one triangle (int2 row/column blocks)
   int tiles_n = -1, tiles_uplo = 0;
   long long tiles_count = 0;
+  int kseg_blocks = 128;            // split form: k-blocks (64 deep) per H/S launch
   // timing
   cudaEvent_t ev[8]{};
   bool events_ready = false;

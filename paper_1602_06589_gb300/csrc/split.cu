@@ -57,6 +57,8 @@ enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPILOGUE
 struct GemmProblem {
   int M, N, K;              // output rows, output complex columns, complex depth
   int a_pps, b_pps;         // planes per slice of the A and B slice arrays
+  int a_nkb, b_nkb;         // k-blocks per plane of the A and B slice arrays
+  int kb_begin;             // first k-block of this problem's depth range (both operands)
   int a_real;               // A has a zero imaginary part: skip the i half
   int uplo;                 // 0, 'U' or 'L' (tile set and write mask)
   int accumulate;           // C += result instead of C = result
@@ -309,14 +311,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
                       break;
                     }
                     const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + 16384;
-                    const int k = kb * BK;
                     const int pa = (p - 1) * pr.a_pps + h;
                     const int pb0 = (q - 1) * pr.b_pps + h;      // h=0: re, h=1: im
                     const int pb1 = (q - 1) * pr.b_pps + h + 1;  // h=0: im, h=1: -re
+                    const int kbA = pr.kb_begin + kb;
+                    const int kbB = pr.kb_begin + ti.b_k0 / BK + kb;  // b_k0 is a multiple of 64
                     mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
-                    tma_load_3d(sA, mA, full0 + 8 * st, k, ti.m0, pa);
-                    tma_load_3d(sB, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb0);
-                    tma_load_3d(sB + 8192, mB, full0 + 8 * st, ti.b_k0 + k, ti.n0, pb1);
+                    tma_load_3d(sA, mA, full0 + 8 * st, 0, ti.m0, pa * pr.a_nkb + kbA);
+                    tma_load_3d(sB, mB, full0 + 8 * st, 0, ti.n0, pb0 * pr.b_nkb + kbB);
+                    tma_load_3d(sB + 8192, mB, full0 + 8 * st, 0, ti.n0, pb1 * pr.b_nkb + kbB);
                   }
               }
             }
@@ -501,9 +504,12 @@ __device__ __forceinline__ long long to_fixed(double v, int shift) {
   return (b < 0) ? -N : N;
 }
 
+// Output layout (k-blocked): plane P, column c, depth k at
+//   dst[P * plane_stride + ((k / 64) * ncols + c) * 64 + k % 64],
+// so one 64-deep block of 128 consecutive columns is 16 KB of contiguous memory.
 __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ src, long long lds, int K,
                                                     const double *__restrict__ urow, int s, int planes,
-                                                    __nv_bfloat16 *__restrict__ dst, long long ldk,
+                                                    __nv_bfloat16 *__restrict__ dst, long long ldk, int ncols,
                                                     long long plane_stride, int *__restrict__ expo) {
   const int col = blockIdx.x;
   const double2 *c = src + (size_t)col * lds;
@@ -528,8 +534,8 @@ __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ 
   }
   __syncthreads();
   const int shift = 7 + 8 * (s - 1) - e_sh;
-  __nv_bfloat16 *out = dst + (size_t)col * ldk;
   for (int k = threadIdx.x; k < (int)ldk; k += blockDim.x) {
+    __nv_bfloat16 *out = dst + ((size_t)(k >> 6) * ncols + col) * 64 + (k & 63);
     long long Nr = 0, Ni = 0;
     if (k < K) {
       double2 v = c[k];
@@ -553,9 +559,9 @@ __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ 
         di = (int)Ni;
       }
       __nv_bfloat16 *base = out + (size_t)(p - 1) * planes * plane_stride;
-      base[k] = __float2bfloat16_rn((float)dr);
-      base[plane_stride + k] = __float2bfloat16_rn((float)di);
-      if (planes == 3) base[2 * plane_stride + k] = __float2bfloat16_rn((float)-dr);
+      base[0] = __float2bfloat16_rn((float)dr);
+      base[plane_stride] = __float2bfloat16_rn((float)di);
+      if (planes == 3) base[2 * plane_stride] = __float2bfloat16_rn((float)-dr);
     }
   }
 }
@@ -582,13 +588,13 @@ EncodeTiledFn encoder() {
   return fn;
 }
 
-// 3D map over bf16 planes [plane][col][k]: k extent `kext`, row stride ldk elements.
-bool make_map(CUtensorMap *m, const void *base, long long kext, long long ncols, long long nplanes, long long ldk,
-              int box_rows) {
+// 3D map over k-blocked bf16 planes: dim0 = 64 (depth inside a block),
+// dim1 = column, dim2 = plane * nkb + k-block; boxes of 64 x box_rows x 1.
+bool make_map(CUtensorMap *m, const void *base, long long nkb, long long ncols, long long nplanes, int box_rows) {
   EncodeTiledFn fn = encoder();
   if (!fn) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)kext, (cuuint64_t)ncols, (cuuint64_t)nplanes};
-  cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(ncols * ldk * 2)};
+  cuuint64_t dims[3] = {(cuuint64_t)BK, (cuuint64_t)ncols, (cuuint64_t)(nkb * nplanes)};
+  cuuint64_t strides[2] = {(cuuint64_t)BK * 2, (cuuint64_t)(ncols * BK * 2)};
   cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
@@ -632,7 +638,7 @@ cudaError_t launch_slice(const double2 *src, long long lds, int K, const double 
                          __nv_bfloat16 *dst, long long ldk, long long plane_stride, int *expo, int ncols,
                          cudaStream_t st) {
   if (ncols <= 0) return cudaSuccess;
-  slice_kernel<<<ncols, 256, 0, st>>>(src, lds, K, urow, s, planes, dst, ldk, plane_stride, expo);
+  slice_kernel<<<ncols, 256, 0, st>>>(src, lds, K, urow, s, planes, dst, ldk, ncols, plane_stride, expo);
   return cudaGetLastError();
 }
 
@@ -793,8 +799,10 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
         pr.tile_list = nullptr;
         pr.tile_begin = tiles;
         tiles += (long long)pr.n_batch * pr.nbm * pr.nbn;
-        if (!make_map(&P.mapA[np], sp.d_Tsl, sp.dpad, sp.dpad, 2LL * slices, sp.dpad, BM) ||
-            !make_map(&P.mapB[np], w.Wsl, w.ldk, n_g, 3LL * slices, w.ldk, BN))
+        pr.a_nkb = sp.dpad / BK;
+        pr.b_nkb = (int)(w.ldk / BK);
+        if (!make_map(&P.mapA[np], sp.d_Tsl, pr.a_nkb, sp.dpad, 2LL * slices, BM) ||
+            !make_map(&P.mapB[np], w.Wsl, pr.b_nkb, n_g, 3LL * slices, BN))
           return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (T-apply)");
       }
       P.nprob = np;
@@ -822,6 +830,13 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       ctx->tiles_uplo = uplo;
       ctx->tiles_count = (long long)tl.size();
     }
+    // The depth is cut into segments run as separate launches that add into
+    // H and S: shorter tiles keep the CTAs of one wave close together in k,
+    // so the A and B blocks they share stay in L2.
+    const int nkb_all = (int)(w.ldk / BK);
+    const int seg_kb = std::max(1, ctx->kseg_blocks);
+    for (int kb0 = 0; kb0 < nkb_all; kb0 += seg_kb) {
+    const int seg = std::min(seg_kb, nkb_all - kb0);
     GemmParams P;
     std::memset(&P, 0, sizeof(P));
     P.s = slices;
@@ -832,13 +847,14 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       GemmProblem &pr = P.prob[k];
       pr.M = n_g;
       pr.N = n_g;
-      pr.K = cdepth;
+      pr.K = seg * BK;
+      pr.kb_begin = kb0;
       pr.a_pps = (k == 0) ? 3 : 2;
       pr.b_pps = 3;
       pr.a_real = 0;
       pr.uplo = uplo;
-      pr.accumulate = accumulate ? 1 : 0;
-      pr.F = fixed_point_bits(cdepth);
+      pr.accumulate = (accumulate || kb0 > 0) ? 1 : 0;
+      pr.F = fixed_point_bits(seg * BK);
       pr.expA = (k == 0) ? w.expW : w.expY;
       pr.expB = (k == 0) ? w.expX : w.expW;
       pr.C = (k == 0) ? H : S;
@@ -853,13 +869,15 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       pr.tile_begin = k * per;
       const void *a = (k == 0) ? (const void *)w.Wsl : (const void *)w.Ysl;
       const void *b = (k == 0) ? (const void *)w.Xsl : (const void *)w.Wsl;
-      if (!make_map(&P.mapA[k], a, w.ldk, n_g, (long long)pr.a_pps * slices, w.ldk, BM) ||
-          !make_map(&P.mapB[k], b, w.ldk, n_g, 3LL * slices, w.ldk, BN))
+      pr.a_nkb = pr.b_nkb = (int)(w.ldk / BK);
+      if (!make_map(&P.mapA[k], a, pr.a_nkb, n_g, (long long)pr.a_pps * slices, BM) ||
+          !make_map(&P.mapB[k], b, pr.b_nkb, n_g, 3LL * slices, BN))
         return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
     }
     P.nprob = 2;
     P.ntiles = 2 * per;
     HSG_LAUNCH(ctx, launch_gemm(P, s));
+    }
   }
   return HSGEN_OK;
 }
