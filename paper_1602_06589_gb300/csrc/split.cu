@@ -44,11 +44,12 @@ namespace {
 
 constexpr int kMaxProb = 4;
 constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int NST = 6;
+constexpr int NST = 7;
 constexpr int STAGE_BYTES = 32768;      // A 128x64 bf16 (16 KB) + B 128x64 bf16 (16 KB)
-constexpr int NTHREADS = 192;
-constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 512;     // acc0 [0,128) acc1 [128,256) wide int64 [256,512)
+constexpr int NTHREADS = 320;           // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int NACC = 4;                 // FP32 accumulator buffers of 128 TMEM columns
+constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 230656 <= 232448 (227 KiB)
+constexpr uint32_t TMEM_COLS = 512;
 // tcgen05 kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
@@ -181,6 +182,23 @@ __device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32])
       : "memory");
 }
 
+// One lane of the (converged) warp; the warp's other lanes skip the guarded
+// block. Issuing tcgen05/TMA work this way keeps the surrounding bookkeeping
+// warp-uniform, so descriptors stay in uniform registers and the issue loop
+// keeps up with the tensor core.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile("{\n .reg .b32 r;\n .reg .pred p;\n elect.sync r|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(pred));
+  return pred != 0;
+}
+// Bounded wait with a warp-uniform verdict (lane 0 waits, the warp follows).
+__device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, unsigned long long timeout_ns) {
+  int got = 0;
+  if ((threadIdx.x & 31) == 0) got = mbar_wait(a, parity, timeout_ns) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, got, 0) != 0;
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 B.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
@@ -251,10 +269,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES);
-  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NST + 5);
+  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NST + 2 * NACC + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NST, accf0 = empty0 + 8 * NST, acce0 = accf0 + 16,
-                 tdown = acce0 + 16;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NST, accf0 = empty0 + 8 * NST,
+                 acce0 = accf0 + 8 * NACC, tdown = acce0 + 8 * NACC;
   const uint32_t sbase = smem_u32(smem);
   const unsigned long long tmo = P.timeout_ns;
 
@@ -263,10 +281,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
       mbar_init(full0 + 8 * i, 1);
       mbar_init(empty0 + 8 * i, 1);
     }
-    mbar_init(accf0, 1);
-    mbar_init(accf0 + 8, 1);
-    mbar_init(acce0, 4);
-    mbar_init(acce0 + 8, 4);
+    for (int i = 0; i < NACC; ++i) {
+      mbar_init(accf0 + 8 * i, 1);
+      mbar_init(acce0 + 8 * i, 8);  // one arrival per epilogue warp
+    }
     mbar_init(tdown, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -285,124 +303,138 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
-    if (lane == 0) {
-      uint32_t it = 0;
-      bool ok = true;
-      for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-        const Tile ti = decode_tile(P, t);
-        const GemmProblem &pr = P.prob[ti.prob];
-        const Sched sc(pr, ti, S);
-        const CUtensorMap *mA = &P.mapA[ti.prob], *mB = &P.mapB[ti.prob];
-        for (int kc = 0; kc < sc.nkc && ok; ++kc) {
-          const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
-          for (int g = 2; g <= S + 1 && ok; ++g) {
-            const int plo = max(1, g - S), phi = min(S, g - 1);
-            for (int pb = plo; pb <= phi && ok; pb += sc.ppc) {
-              const int pe = min(phi, pb + sc.ppc - 1);
-              for (int p = pb; p <= pe && ok; ++p) {
-                const int q = g - p;
-                for (int kb = kb0; kb < kb1 && ok; ++kb)
-                  for (int h = 0; h < sc.halves; ++h, ++it) {
-                    const int st = it % NST;
-                    const uint32_t round = it / NST;
-                    if (!mbar_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
-                      atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
-                      ok = false;
-                      break;
-                    }
-                    const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + 16384;
-                    const int pa = (p - 1) * pr.a_pps + h;
-                    const int pb0 = (q - 1) * pr.b_pps + h;      // h=0: re, h=1: im
-                    const int pb1 = (q - 1) * pr.b_pps + h + 1;  // h=0: im, h=1: -re
-                    const int kbA = pr.kb_begin + kb;
-                    const int kbB = pr.kb_begin + ti.b_k0 / BK + kb;  // b_k0 is a multiple of 64
+    uint32_t it = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      const Tile ti = decode_tile(P, t);
+      const GemmProblem &pr = P.prob[ti.prob];
+      const Sched sc(pr, ti, S);
+      const CUtensorMap *mA = &P.mapA[ti.prob], *mB = &P.mapB[ti.prob];
+      for (int kc = 0; kc < sc.nkc && ok; ++kc) {
+        const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
+        for (int g = 2; g <= S + 1 && ok; ++g) {
+          const int plo = max(1, g - S), phi = min(S, g - 1);
+          for (int pb = plo; pb <= phi && ok; pb += sc.ppc) {
+            const int pe = min(phi, pb + sc.ppc - 1);
+            for (int p = pb; p <= pe && ok; ++p) {
+              const int q = g - p;
+              for (int kb = kb0; kb < kb1 && ok; ++kb)
+                for (int h = 0; h < sc.halves; ++h, ++it) {
+                  const int st = it % NST;
+                  const uint32_t round = it / NST;
+                  if (!warp_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
+                    if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
+                    ok = false;
+                    break;
+                  }
+                  const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + 16384;
+                  const int pa = (p - 1) * pr.a_pps + h;
+                  const int pb0 = (q - 1) * pr.b_pps + h;      // h=0: re, h=1: im
+                  const int pb1 = (q - 1) * pr.b_pps + h + 1;  // h=0: im, h=1: -re
+                  const int kbA = pr.kb_begin + kb;
+                  const int kbB = pr.kb_begin + ti.b_k0 / BK + kb;  // b_k0 is a multiple of 64
+                  if (elect_one()) {
                     mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
                     tma_load_3d(sA, mA, full0 + 8 * st, 0, ti.m0, pa * pr.a_nkb + kbA);
                     tma_load_3d(sB, mB, full0 + 8 * st, 0, ti.n0, pb0 * pr.b_nkb + kbB);
                     tma_load_3d(sB + 8192, mB, full0 + 8 * st, 0, ti.n0, pb1 * pr.b_nkb + kbB);
                   }
-              }
+                  __syncwarp();
+                }
             }
           }
         }
       }
-      // no copy may still be in flight at teardown: the latest use of every
-      // stage must have landed (bounded)
-      for (int st = 0; st < NST; ++st) {
-        if (it <= (uint32_t)st) break;
-        const uint32_t j = st + NST * ((it - 1 - st) / NST);
-        if (!mbar_wait(full0 + 8 * st, (j / NST) & 1, drain)) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
-      }
+    }
+    // no copy may still be in flight at teardown: the latest use of every
+    // stage must have landed (bounded)
+    for (int st = 0; st < NST; ++st) {
+      if (it <= (uint32_t)st) break;
+      const uint32_t j = st + NST * ((it - 1 - st) / NST);
+      if (!warp_wait(full0 + 8 * st, (j / NST) & 1, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
     }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer --------------------------------
-    if (lane == 0) {
-      uint32_t it = 0, cc = 0;
-      bool ok = true;
-      for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
-        const Tile ti = decode_tile(P, t);
-        const GemmProblem &pr = P.prob[ti.prob];
-        const Sched sc(pr, ti, S);
-        for (int kc = 0; kc < sc.nkc && ok; ++kc) {
-          const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
-          for (int g = 2; g <= S + 1 && ok; ++g) {
-            const int plo = max(1, g - S), phi = min(S, g - 1);
-            for (int pb = plo; pb <= phi && ok; pb += sc.ppc, ++cc) {
-              const int pe = min(phi, pb + sc.ppc - 1);
-              const int buf = cc & 1;
-              const uint32_t use = cc >> 1;
-              if (!mbar_wait(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
-                atomicOr(P.status, ERR_TIMEOUT_MMA);
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t dacc = tbase + buf * 128;
-              bool first = true;
-              for (int p = pb; p <= pe && ok; ++p)
-                for (int kb = kb0; kb < kb1 && ok; ++kb)
-                  for (int h = 0; h < sc.halves; ++h, ++it) {
-                    const int st = it % NST;
-                    if (!mbar_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
-                      atomicOr(P.status, ERR_TIMEOUT_MMA);
-                      ok = false;
-                      break;
-                    }
-                    tc_fence_after();
-                    const uint64_t da = desc_sw128(sbase + st * STAGE_BYTES);
-                    const uint64_t db = desc_sw128(sbase + st * STAGE_BYTES + 16384);
+    const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + 16384);
+    uint32_t it = 0, cc = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      const Tile ti = decode_tile(P, t);
+      const GemmProblem &pr = P.prob[ti.prob];
+      const Sched sc(pr, ti, S);
+      for (int kc = 0; kc < sc.nkc && ok; ++kc) {
+        const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
+        for (int g = 2; g <= S + 1 && ok; ++g) {
+          const int plo = max(1, g - S), phi = min(S, g - 1);
+          for (int pb = plo; pb <= phi && ok; pb += sc.ppc, ++cc) {
+            const int pe = min(phi, pb + sc.ppc - 1);
+            const int buf = cc % NACC;
+            const uint32_t use = cc / NACC;
+            if (!warp_wait(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
+              if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dacc = tbase + buf * 128;
+            uint32_t accum = 0;
+            for (int p = pb; p <= pe && ok; ++p)
+              for (int kb = kb0; kb < kb1 && ok; ++kb)
+                for (int h = 0; h < sc.halves; ++h, ++it) {
+                  const int st = it % NST;
+                  if (!warp_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
+                    if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
+                    ok = false;
+                    break;
+                  }
+                  tc_fence_after();
+                  const uint64_t da = descA0 + (uint64_t)(st * (STAGE_BYTES >> 4));
+                  const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4));
+                  if (elect_one()) {
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) tc_mma(dacc, da + 2 * kk, db + 2 * kk, (first && kk == 0) ? 0u : 1u);
-                    first = false;
+                    for (int kk = 0; kk < BK / 16; ++kk) tc_mma(dacc, da + 2 * kk, db + 2 * kk, (accum | kk) ? 1u : 0u);
                     tc_commit(empty0 + 8 * st);
                   }
-              if (ok) tc_commit(accf0 + 8 * buf);
+                  __syncwarp();
+                  accum = 1;
+                }
+            if (ok) {
+              if (elect_one()) tc_commit(accf0 + 8 * buf);
+              __syncwarp();
             }
           }
         }
       }
-      // every MMA issued has completed before TMEM is released (bounded)
-      tc_commit(tdown);
-      if (!mbar_wait(tdown, 0, drain)) atomicOr(P.status, ERR_TIMEOUT_MMA);
     }
+    // every MMA issued has completed before TMEM is released (bounded)
+    if (elect_one()) tc_commit(tdown);
+    __syncwarp();
+    if (!warp_wait(tdown, 0, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
   } else {
     // ------------------------------ epilogue ----------------------------------
-    const int qd = warp & 3;  // TMEM lane quadrant of this warp
+    // Eight warps: warp w reads TMEM lane quadrant w % 4 (rows), and half hf of
+    // the accumulator columns (hf 0: real parts, hf 1: imaginary parts of the
+    // tile's 64 complex columns). The int64 fixed-point sums live in registers
+    // for the whole tile.
+    const int ew = warp - 2;
+    const int qd = warp & 3;
+    const int hf = ew >> 2;
     const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
-    const uint32_t twide = tbase + lane_off + 256;
     uint32_t cc = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const Tile ti = decode_tile(P, t);
       const GemmProblem &pr = P.prob[ti.prob];
       const Sched sc(pr, ti, S);
-      bool first_chunk = true;
+      long long acc[64];
+#pragma unroll
+      for (int u = 0; u < 64; ++u) acc[u] = 0;
       for (int kc = 0; kc < sc.nkc && ok; ++kc)
         for (int g = 2; g <= S + 1 && ok; ++g) {
           const int plo = max(1, g - S), phi = min(S, g - 1);
           for (int pb = plo; pb <= phi && ok; pb += sc.ppc, ++cc) {
-            const int buf = cc & 1;
-            const uint32_t use = cc >> 1;
+            const int buf = cc % NACC;
+            const uint32_t use = cc / NACC;
             // one lane waits, the whole warp follows its verdict (the TMEM loads
             // below are warp-collective)
             int got = 0;
@@ -417,66 +449,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
             const int sh = pr.F - 8 * (g - 2);
             const int ish = sh > 0 ? sh : 0;
             const float fsc = (sh < 0) ? __int_as_float((127 + sh) << 23) : 1.0f;
-            const uint32_t tacc = tbase + lane_off + buf * 128;
-#pragma unroll 1
-            for (int c0 = 0; c0 < 128; c0 += 16) {
-              uint32_t v[16], w[32];
-              tc_ld16(tacc + c0, v);
-              if (!first_chunk) tc_ld32(twide + 2 * c0, w);
+            const uint32_t tacc = tbase + lane_off + buf * 128 + hf * 64;
+            uint32_t v[32];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              tc_ld32(tacc + half * 32, v);
               tc_wait_ld();
 #pragma unroll
-              for (int u = 0; u < 16; ++u) {
-                long long x = first_chunk ? 0LL : (long long)(((unsigned long long)w[2 * u + 1] << 32) | w[2 * u]);
-                const int vi = __float2int_rn(__uint_as_float(v[u]) * fsc);
-                x += (long long)vi << ish;
-                w[2 * u] = (uint32_t)(unsigned long long)x;
-                w[2 * u + 1] = (uint32_t)((unsigned long long)x >> 32);
-              }
-              tc_st32(twide + 2 * c0, w);
+              for (int u = 0; u < 32; ++u)
+                acc[half * 32 + u] += (long long)__float2int_rn(__uint_as_float(v[u]) * fsc) << ish;
             }
-            tc_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * buf);
-            first_chunk = false;
           }
         }
       if (!ok) break;
       // ---- tile output: int64 fixed point -> FP64, scaled by 2^(eA + eB - 14 - F)
-      const int rl = qd * 32 + lane;
-      const int row = ti.m0 + rl;  // row within the problem
-      const bool rvalid = row < pr.M;
-      const int eA = rvalid ? pr.expA[row] : 0;
-      const long long grow = (long long)ti.c_row0 + row;  // row in C
-#pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        uint32_t wr[32], wi[32];
-        tc_ld32(twide + 2 * c0, wr);
-        tc_ld32(twide + 2 * (c0 + 64), wi);
-        tc_wait_ld();
-        if (!rvalid) continue;
+      const int row = ti.m0 + qd * 32 + lane;  // row within the problem
+      if (row < pr.M) {
+        const int eA = pr.expA[row];
+        const long long grow = (long long)ti.c_row0 + row;  // row in C
+        double *Cd = (double *)pr.C + 2 * grow + hf;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int col = ti.n0 + c0 + u;
-          const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
-          if (!keep) continue;
-          const long long xr = (long long)(((unsigned long long)wr[2 * u + 1] << 32) | wr[2 * u]);
-          const long long xi = (long long)(((unsigned long long)wi[2 * u + 1] << 32) | wi[2 * u]);
-          const int e = eA + pr.expB[col] - 14 - pr.F;
-          const double scl =
-              (e > -1022 && e < 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
-          double re = __ll2double_rn(xr) * scl, im = __ll2double_rn(xi) * scl;
-          double2 *dst = pr.C + (size_t)col * pr.ldc + grow;
-          if (pr.accumulate) {
-            const double2 o = *dst;
-            re += o.x;
-            im += o.y;
+        for (int u0 = 0; u0 < 64; u0 += 16) {
+          // previous values first (independent loads in flight together), then the stores
+          double old[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int col = ti.n0 + u0 + u;
+            const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
+            old[u] = (keep && pr.accumulate) ? Cd[2 * (size_t)col * pr.ldc] : 0.0;
           }
-          if (pr.uplo && row == col) im = 0.0;
-          *dst = make_double2(re, im);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int col = ti.n0 + u0 + u;
+            const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
+            if (!keep) continue;
+            const int e = eA + pr.expB[col] - 14 - pr.F;
+            const double scl =
+                (e > -1022 && e < 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+            double x = __ll2double_rn(acc[u0 + u]) * scl + old[u];
+            if (hf == 1 && pr.uplo && row == col) x = 0.0;
+            Cd[2 * (size_t)col * pr.ldc] = x;
+          }
         }
       }
-      tc_fence_before();
     }
   }
   tc_fence_before();
