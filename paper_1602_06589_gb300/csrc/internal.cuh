@@ -75,6 +75,10 @@ struct hsgen_ctx {
   int tiles_n = -1, tiles_uplo = 0;
   long long tiles_count = 0;
   int kseg_blocks = 128;            // split form: k-blocks (64 deep) per H/S launch
+  hsg::Workspace ws_batch;          // batched k-points: per-k slices, tables, shared scratch
+  cudaGraphExec_t batch_exec = nullptr;  // captured kernel sequence of the last batch
+  cudaStream_t capture_stream = nullptr; // private stream the batch sequence is captured on
+  std::vector<long long> batch_key;      // what that graph was captured for
   // timing
   cudaEvent_t ev[8]{};
   bool events_ready = false;

@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -79,6 +80,10 @@ struct GemmParams {
   CUtensorMap mapA[kMaxProb];
   CUtensorMap mapB[kMaxProb];
   GemmProblem prob[kMaxProb];
+  // grouped launches (many k-points): problems and maps in device memory
+  // (gmap[2i] = A map, gmap[2i+1] = B map of problem i); null: use the arrays above
+  const GemmProblem *gprob;
+  const CUtensorMap *gmap;
   int nprob;
   long long ntiles;
   int s;
@@ -217,10 +222,23 @@ struct Tile {
   int prob, m0, n0, b_k0, c_row0, nkb;
 };
 
+__device__ __forceinline__ const GemmProblem &problem(const GemmParams &P, int i) {
+  return P.gprob ? P.gprob[i] : P.prob[i];
+}
+__device__ __forceinline__ const CUtensorMap *map_a(const GemmParams &P, int i) {
+  return P.gprob ? &P.gmap[2 * i] : &P.mapA[i];
+}
+__device__ __forceinline__ const CUtensorMap *map_b(const GemmParams &P, int i) {
+  return P.gprob ? &P.gmap[2 * i + 1] : &P.mapB[i];
+}
+
 __device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
-  int pi = 0;
-  while (pi + 1 < P.nprob && t >= P.prob[pi + 1].tile_begin) ++pi;
-  const GemmProblem &pr = P.prob[pi];
+  int pi = 0, hi = P.nprob;  // last problem with tile_begin <= t
+  while (hi - pi > 1) {
+    const int mid = (pi + hi) >> 1;
+    if (problem(P, mid).tile_begin <= t) pi = mid; else hi = mid;
+  }
+  const GemmProblem &pr = problem(P, pi);
   long long lt = t - pr.tile_begin;
   Tile ti;
   ti.prob = pi;
@@ -307,9 +325,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     bool ok = true;
     for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const Tile ti = decode_tile(P, t);
-      const GemmProblem &pr = P.prob[ti.prob];
+      const GemmProblem &pr = problem(P, ti.prob);
       const Sched sc(pr, ti, S);
-      const CUtensorMap *mA = &P.mapA[ti.prob], *mB = &P.mapB[ti.prob];
+      const CUtensorMap *mA = map_a(P, ti.prob), *mB = map_b(P, ti.prob);
       for (int kc = 0; kc < sc.nkc && ok; ++kc) {
         const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
         for (int g = 2; g <= S + 1 && ok; ++g) {
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     bool ok = true;
     for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const Tile ti = decode_tile(P, t);
-      const GemmProblem &pr = P.prob[ti.prob];
+      const GemmProblem &pr = problem(P, ti.prob);
       const Sched sc(pr, ti, S);
       for (int kc = 0; kc < sc.nkc && ok; ++kc) {
         const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     bool ok = true;
     for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       const Tile ti = decode_tile(P, t);
-      const GemmProblem &pr = P.prob[ti.prob];
+      const GemmProblem &pr = problem(P, ti.prob);
       const Sched sc(pr, ti, S);
       long long acc[64];
 #pragma unroll
@@ -708,6 +726,108 @@ std::vector<int2> tri_tiles(int n, int uplo) {
   return out;
 }
 
+// X_a = T_a W_a for the atoms [a0, a1) (one launch per kMaxProb species).
+hsgen_status tapply_split(hsgen_ctx *ctx, int n_g, int a0, int a1, const __nv_bfloat16 *Wsl, long long ldk,
+                          const int *expW, double2 *X, long long ldw, int slices, cudaStream_t s) {
+  const int row_base = ctx->off[a0];
+  std::vector<int> species;
+  std::vector<std::pair<int, int>> ranges;
+  for (int t = 0; t < (int)ctx->types.size(); ++t) {
+    const auto &lst = ctx->atoms_of_type[t];
+    int lo = 0;
+    while (lo < (int)lst.size() && lst[lo] < a0) ++lo;
+    int hi = lo;
+    while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
+    if (hi > lo) {
+      species.push_back(t);
+      ranges.push_back({lo, hi});
+    }
+  }
+  for (size_t b0 = 0; b0 < species.size(); b0 += kMaxProb) {
+    GemmParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.s = slices;
+    P.status = ctx->d_status;
+    P.timeout_ns = (unsigned long long)ctx->opt.wait_timeout_ns;
+    long long tiles = 0;
+    int np = 0;
+    for (size_t b = b0; b < species.size() && np < kMaxProb; ++b, ++np) {
+      const Species &sp = ctx->types[species[b]];
+      GemmProblem &pr = P.prob[np];
+      pr.M = sp.dpad;
+      pr.N = n_g;
+      pr.K = sp.dpad;
+      pr.kb_begin = 0;
+      pr.a_pps = 2;
+      pr.b_pps = 3;
+      pr.a_real = sp.t_real;
+      pr.uplo = 0;
+      pr.accumulate = 0;
+      pr.F = fixed_point_bits(sp.dpad);
+      pr.expA = sp.d_Texp;
+      pr.expB = expW;
+      pr.C = X;
+      pr.ldc = ldw;
+      pr.atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[species[b]] + ranges[b].first;
+      pr.off = ctx->d_off;
+      pr.row_base = row_base;
+      pr.n_batch = ranges[b].second - ranges[b].first;
+      pr.nbm = (sp.dpad + BM - 1) / BM;
+      pr.nbn = (n_g + BN - 1) / BN;
+      pr.tile_list = nullptr;
+      pr.tile_begin = tiles;
+      tiles += (long long)pr.n_batch * pr.nbm * pr.nbn;
+      pr.a_nkb = sp.dpad / BK;
+      pr.b_nkb = (int)(ldk / BK);
+      if (!make_map(&P.mapA[np], sp.d_Tsl, pr.a_nkb, sp.dpad, 2LL * slices, BM) ||
+          !make_map(&P.mapB[np], Wsl, pr.b_nkb, n_g, 3LL * slices, BN))
+        return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (T-apply)");
+    }
+    P.nprob = np;
+    P.ntiles = tiles;
+    HSG_LAUNCH(ctx, launch_gemm(P, s));
+  }
+  return HSGEN_OK;
+}
+
+// One H problem (H = W^H X) and one S problem (S = (U W)^H W) of one k-point
+// over the depth segment [kb0, kb0 + seg) of 64-deep blocks.
+bool hs_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, long long ldk, int kb0, int seg,
+                 bool accumulate, int uplo, const __nv_bfloat16 *Wsl, const __nv_bfloat16 *Xsl,
+                 const __nv_bfloat16 *Ysl, const int *expW, const int *expX, const int *expY, double2 *H, double2 *S,
+                 long long ld, const int2 *tiles, long long ntiles, long long tile_begin, int slices) {
+  for (int k = 0; k < 2; ++k) {
+    GemmProblem &q = pr[k];
+    std::memset(&q, 0, sizeof(q));
+    q.M = n_g;
+    q.N = n_g;
+    q.K = seg * BK;
+    q.kb_begin = kb0;
+    q.a_pps = (k == 0) ? 3 : 2;
+    q.b_pps = 3;
+    q.a_real = 0;
+    q.uplo = uplo;
+    q.accumulate = (accumulate || kb0 > 0) ? 1 : 0;
+    q.F = fixed_point_bits(seg * BK);
+    q.expA = (k == 0) ? expW : expY;
+    q.expB = (k == 0) ? expX : expW;
+    q.C = (k == 0) ? H : S;
+    q.ldc = ld;
+    q.n_batch = 1;
+    q.nbm = (n_g + BM - 1) / BM;
+    q.nbn = (n_g + BN - 1) / BN;
+    q.tile_list = tiles;
+    q.tile_begin = tile_begin + k * ntiles;
+    q.a_nkb = q.b_nkb = (int)(ldk / BK);
+    const void *a = (k == 0) ? (const void *)Wsl : (const void *)Ysl;
+    const void *b = (k == 0) ? (const void *)Xsl : (const void *)Wsl;
+    if (!make_map(&mA[k], a, q.a_nkb, n_g, (long long)q.a_pps * slices, BM) ||
+        !make_map(&mB[k], b, q.b_nkb, n_g, 3LL * slices, BN))
+      return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 int choose_slices(double target_rel_err, int override_slices) {
@@ -771,62 +891,8 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
   HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, nullptr, slices, 3, w.Wsl, w.ldk, plane, w.expW, n_g, s));
   // (2) X_a = T W_a, species by species (up to kMaxProb per launch)
   {
-    std::vector<int> species;
-    std::vector<std::pair<int, int>> ranges;
-    for (int t = 0; t < (int)ctx->types.size(); ++t) {
-      const auto &lst = ctx->atoms_of_type[t];
-      int lo = 0;
-      while (lo < (int)lst.size() && lst[lo] < a0) ++lo;
-      int hi = lo;
-      while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
-      if (hi > lo) {
-        species.push_back(t);
-        ranges.push_back({lo, hi});
-      }
-    }
-    for (size_t b0 = 0; b0 < species.size(); b0 += kMaxProb) {
-      GemmParams P;
-      std::memset(&P, 0, sizeof(P));
-      P.s = slices;
-      P.status = ctx->d_status;
-      P.timeout_ns = tmo;
-      long long tiles = 0;
-      int np = 0;
-      for (size_t b = b0; b < species.size() && np < kMaxProb; ++b, ++np) {
-        const Species &sp = ctx->types[species[b]];
-        GemmProblem &pr = P.prob[np];
-        pr.M = sp.dpad;
-        pr.N = n_g;
-        pr.K = sp.dpad;
-        pr.a_pps = 2;
-        pr.b_pps = 3;
-        pr.a_real = sp.t_real;
-        pr.uplo = 0;
-        pr.accumulate = 0;
-        pr.F = fixed_point_bits(sp.dpad);
-        pr.expA = sp.d_Texp;
-        pr.expB = w.expW;
-        pr.C = X;
-        pr.ldc = ldw;
-        pr.atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[species[b]] + ranges[b].first;
-        pr.off = ctx->d_off;
-        pr.row_base = row_base;
-        pr.n_batch = ranges[b].second - ranges[b].first;
-        pr.nbm = (sp.dpad + BM - 1) / BM;
-        pr.nbn = (n_g + BN - 1) / BN;
-        pr.tile_list = nullptr;
-        pr.tile_begin = tiles;
-        tiles += (long long)pr.n_batch * pr.nbm * pr.nbn;
-        pr.a_nkb = sp.dpad / BK;
-        pr.b_nkb = (int)(w.ldk / BK);
-        if (!make_map(&P.mapA[np], sp.d_Tsl, pr.a_nkb, sp.dpad, 2LL * slices, BM) ||
-            !make_map(&P.mapB[np], w.Wsl, pr.b_nkb, n_g, 3LL * slices, BN))
-          return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (T-apply)");
-      }
-      P.nprob = np;
-      P.ntiles = tiles;
-      HSG_LAUNCH(ctx, launch_gemm(P, s));
-    }
+    hsgen_status st = tapply_split(ctx, n_g, a0, a1, w.Wsl, w.ldk, w.expW, X, ldw, slices, s);
+    if (st != HSGEN_OK) return st;
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
   // (3) X slices (right operand of H) and (U W) slices (left operand of S)
@@ -861,37 +927,9 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
     P.status = ctx->d_status;
     P.timeout_ns = tmo;
     const long long per = ctx->tiles_count;
-    for (int k = 0; k < 2; ++k) {
-      GemmProblem &pr = P.prob[k];
-      pr.M = n_g;
-      pr.N = n_g;
-      pr.K = seg * BK;
-      pr.kb_begin = kb0;
-      pr.a_pps = (k == 0) ? 3 : 2;
-      pr.b_pps = 3;
-      pr.a_real = 0;
-      pr.uplo = uplo;
-      pr.accumulate = (accumulate || kb0 > 0) ? 1 : 0;
-      pr.F = fixed_point_bits(seg * BK);
-      pr.expA = (k == 0) ? w.expW : w.expY;
-      pr.expB = (k == 0) ? w.expX : w.expW;
-      pr.C = (k == 0) ? H : S;
-      pr.ldc = ld;
-      pr.atoms = nullptr;
-      pr.off = nullptr;
-      pr.row_base = 0;
-      pr.n_batch = 1;
-      pr.nbm = (n_g + BM - 1) / BM;
-      pr.nbn = (n_g + BN - 1) / BN;
-      pr.tile_list = (const int2 *)ctx->d_tiles;
-      pr.tile_begin = k * per;
-      const void *a = (k == 0) ? (const void *)w.Wsl : (const void *)w.Ysl;
-      const void *b = (k == 0) ? (const void *)w.Xsl : (const void *)w.Wsl;
-      pr.a_nkb = pr.b_nkb = (int)(w.ldk / BK);
-      if (!make_map(&P.mapA[k], a, pr.a_nkb, n_g, (long long)pr.a_pps * slices, BM) ||
-          !make_map(&P.mapB[k], b, pr.b_nkb, n_g, 3LL * slices, BN))
-        return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
-    }
+    if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, w.ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
+                     w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles, per, 0, slices))
+      return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
     P.nprob = 2;
     P.ntiles = 2 * per;
     HSG_LAUNCH(ctx, launch_gemm(P, s));
@@ -913,9 +951,257 @@ hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s) {
   return HSGEN_OK;
 }
 
-hsgen_status split_batched(hsgen_ctx *, int, const int *, const double *const *, void *const *, void *const *,
-                           const long long *, cudaStream_t) {
-  return HSGEN_ENOTSUP;
+// Many k-points (D22): per k-point the cheap steps (radial factors,
+// coefficients, slicing, X = T W) fill that k-point's slice buffers; then one
+// persistent grouped launch per depth segment runs the H and S tiles of every
+// k-point of a group (uneven N_G and mixed l_max share one tile queue). The
+// whole kernel sequence is captured once into a CUDA graph and replayed while
+// the batch (sizes and output pointers) stays the same.
+hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec, void *const *H,
+                           void *const *S, const long long *ld, cudaStream_t s) {
+  if (ctx->opt.precision != HSGEN_SPLIT) return HSGEN_ENOTSUP;
+  const int na = (int)ctx->toa.size();
+  if (ctx->opt.atom_chunk > 0 && ctx->opt.atom_chunk < na) return HSGEN_ENOTSUP;
+  if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: no system set");
+  if (ctx->opt.fill_full) return HSGEN_ENOTSUP;
+  for (int k = 0; k < n_k; ++k) {
+    if (n_g[k] < 0 || ld[k] < n_g[k] || (n_g[k] > 0 && (!kvec[k] || !H[k] || !S[k])))
+      return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: bad size, leading dimension or pointer");
+    if (n_g[k] > 0) {
+      for (int i = 0; i < 3 * n_g[k]; ++i)
+        if (!std::isfinite(kvec[k][i])) return set_err(ctx, HSGEN_ENUMERIC, "build_HS_batched: non-finite kvec");
+    }
+  }
+  const int slices = choose_slices(ctx->opt.target_rel_err, ctx->opt.slices);
+  if (ctx->split_slices != slices) {
+    hsgen_status st = split_prepare_types(ctx, slices);
+    if (st != HSGEN_OK) return st;
+  }
+  HSG_CUDA(ctx, cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  const int depth = ctx->depth;
+  const long long ldk = round_up(depth, BK);
+  const int nt = (int)ctx->types.size();
+  const int uplo = ctx->opt.uplo;
+  const int nkb_all = (int)(ldk / BK), seg_kb = std::max(1, ctx->kseg_blocks);
+  const int nseg = (nkb_all + seg_kb - 1) / seg_kb;
+  auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
+  // ---- plan: groups of k-points whose slices fit the budget
+  size_t budget = (size_t)96 << 30;
+  if (const char *e = std::getenv("HSGEN_BATCH_BYTES")) budget = (size_t)std::max(1.0, std::atof(e));
+  std::vector<size_t> kslice(n_k);
+  int max_ng = 1;
+  long long sum_ng = 0;
+  for (int k = 0; k < n_k; ++k) {
+    kslice[k] = al((size_t)8 * slices * n_g[k] * ldk * sizeof(__nv_bfloat16));
+    max_ng = std::max(max_ng, n_g[k]);
+    sum_ng += n_g[k];
+  }
+  std::vector<std::pair<int, int>> groups;
+  for (int k = 0; k < n_k;) {
+    size_t acc = 0;
+    int k1 = k;
+    while (k1 < n_k && (k1 == k || acc + kslice[k1] <= budget)) acc += kslice[k1++];
+    groups.push_back({k, k1});
+    k = k1;
+  }
+  // ---- tile lists per k-point (host) and table sizes
+  std::vector<std::vector<int2>> tl(n_k);
+  size_t n_tl = 0;
+  for (int k = 0; k < n_k; ++k) {
+    if (n_g[k] > 0) tl[k] = tri_tiles(n_g[k], uplo);
+    n_tl += tl[k].size();
+  }
+  // ---- workspace layout
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t r = o;
+    o += al(b);
+    return r;
+  };
+  const size_t o_kv = take(sizeof(double) * 3 * (size_t)std::max<long long>(sum_ng, 1));
+  const size_t o_F = take(sizeof(double2) * (size_t)nt * max_ng * kRadStride);
+  const size_t o_W = take(sizeof(double2) * (size_t)depth * max_ng);
+  const size_t o_X = take(sizeof(double2) * (size_t)depth * max_ng);
+  size_t max_group = 0;
+  for (auto &g : groups) {
+    size_t b = 0;
+    for (int k = g.first; k < g.second; ++k) b += kslice[k];
+    max_group = std::max(max_group, b);
+  }
+  const size_t o_sl = take(max_group);
+  const size_t o_exp = take(sizeof(int) * 3 * (size_t)std::max<long long>(sum_ng, 1));
+  const size_t o_tl = take(sizeof(int2) * std::max<size_t>(n_tl, 1));
+  const size_t n_tab = (size_t)2 * n_k * nseg;  // problems over all groups and segments
+  const size_t o_prob = take(sizeof(GemmProblem) * n_tab);
+  const size_t o_map = take(sizeof(CUtensorMap) * 2 * n_tab);
+  const size_t total = o;
+  if (ctx->ws_batch.bytes < total) {
+    if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+    ctx->batch_exec = nullptr;
+    ctx->batch_key.clear();
+    if (ctx->ws_batch.ptr) cudaFree(ctx->ws_batch.ptr);
+    ctx->ws_batch.ptr = nullptr;
+    ctx->ws_batch.bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->ws_batch.ptr, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_err(ctx, e, "cudaMalloc(batched workspace)");
+    }
+    ctx->ws_batch.bytes = total;
+  }
+  char *ws = (char *)ctx->ws_batch.ptr;
+  double *d_kv = (double *)(ws + o_kv);
+  double2 *F = (double2 *)(ws + o_F), *W = (double2 *)(ws + o_W), *X = (double2 *)(ws + o_X);
+  int *d_exp = (int *)(ws + o_exp);
+  int2 *d_tl = (int2 *)(ws + o_tl);
+  GemmProblem *d_prob = (GemmProblem *)(ws + o_prob);
+  CUtensorMap *d_map = (CUtensorMap *)(ws + o_map);
+  // ---- per k-point offsets
+  std::vector<long long> kv_off(n_k + 1, 0), tl_off(n_k + 1, 0);
+  for (int k = 0; k < n_k; ++k) {
+    kv_off[k + 1] = kv_off[k] + n_g[k];
+    tl_off[k + 1] = tl_off[k] + (long long)tl[k].size();
+  }
+  auto slice_base = [&](int k, int g) {
+    size_t b = 0;
+    for (int j = groups[g].first; j < k; ++j) b += kslice[j];
+    return (__nv_bfloat16 *)(ws + o_sl + b);
+  };
+  // ---- uploads (outside any capture): k vectors, tile lists, problem/map tables
+  for (int k = 0; k < n_k; ++k)
+    if (n_g[k] > 0)
+      HSG_CUDA(ctx, cudaMemcpyAsync(d_kv + 3 * kv_off[k], kvec[k], sizeof(double) * 3 * n_g[k],
+                                    cudaMemcpyHostToDevice, s));
+  std::vector<int2> tl_all;
+  tl_all.reserve(n_tl);
+  for (int k = 0; k < n_k; ++k) tl_all.insert(tl_all.end(), tl[k].begin(), tl[k].end());
+  if (n_tl) HSG_CUDA(ctx, cudaMemcpyAsync(d_tl, tl_all.data(), sizeof(int2) * n_tl, cudaMemcpyHostToDevice, s));
+  std::vector<GemmProblem> hprob(n_tab);
+  std::vector<CUtensorMap> hmap(2 * n_tab);
+  std::vector<long long> launch_tiles;  // per (group, segment)
+  std::vector<size_t> launch_first;     // first problem index per (group, segment)
+  std::vector<int> launch_nprob;
+  size_t pi = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi)
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int kb0 = sg * seg_kb, seg = std::min(seg_kb, nkb_all - kb0);
+      launch_first.push_back(pi);
+      long long tiles = 0;
+      int np = 0;
+      for (int k = groups[gi].first; k < groups[gi].second; ++k) {
+        if (n_g[k] <= 0) continue;
+        const long long plane = (long long)n_g[k] * ldk;
+        __nv_bfloat16 *Wsl = slice_base(k, (int)gi), *Xsl = Wsl + 3 * slices * plane, *Ysl = Xsl + 3 * slices * plane;
+        int *eW = d_exp + 3 * kv_off[k], *eX = eW + n_g[k], *eY = eX + n_g[k];
+        GemmProblem pr2[2];
+        CUtensorMap ma[2], mb[2];
+        const long long nt_k = (long long)tl[k].size();
+        if (!hs_problems(pr2, ma, mb, n_g[k], ldk, kb0, seg, false, uplo, Wsl, Xsl, Ysl, eW, eX, eY,
+                         (double2 *)H[k], (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k, tiles, slices))
+          return set_err(ctx, HSGEN_ECUDA, "batched: cuTensorMapEncodeTiled failed");
+        for (int j = 0; j < 2; ++j) {
+          hprob[pi] = pr2[j];
+          hmap[2 * pi] = ma[j];
+          hmap[2 * pi + 1] = mb[j];
+          ++pi;
+          ++np;
+        }
+        tiles += 2 * nt_k;
+      }
+      launch_tiles.push_back(tiles);
+      launch_nprob.push_back(np);
+    }
+  if (pi) {
+    HSG_CUDA(ctx, cudaMemcpyAsync(d_prob, hprob.data(), sizeof(GemmProblem) * pi, cudaMemcpyHostToDevice, s));
+    HSG_CUDA(ctx, cudaMemcpyAsync(d_map, hmap.data(), sizeof(CUtensorMap) * 2 * pi, cudaMemcpyHostToDevice, s));
+  }
+  // ---- the kernel sequence, captured once
+  std::vector<long long> key = {(long long)(uintptr_t)ws, (long long)slices, (long long)uplo, (long long)n_k};
+  for (int k = 0; k < n_k; ++k) {
+    key.push_back(n_g[k]);
+    key.push_back(ld[k]);
+    key.push_back((long long)(uintptr_t)H[k]);
+    key.push_back((long long)(uintptr_t)S[k]);
+  }
+  if (!(ctx->batch_exec && ctx->batch_key == key)) {
+    if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+    ctx->batch_exec = nullptr;
+    ctx->batch_key.clear();
+    // Captured on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph then runs on the caller's.
+    if (!ctx->capture_stream)
+      HSG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    const cudaStream_t caller = s;
+    s = ctx->capture_stream;
+    HSG_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    hsgen_status st = HSGEN_OK;
+    ctx->launches = 0;
+    auto body = [&]() -> hsgen_status {
+      for (size_t gi = 0; gi < groups.size(); ++gi) {
+        for (int k = groups[gi].first; k < groups[gi].second; ++k) {
+          const int ng = n_g[k];
+          if (ng <= 0) continue;
+          const double *kd = d_kv + 3 * kv_off[k];
+          const long long plane = (long long)ng * ldk;
+          __nv_bfloat16 *Wsl = slice_base(k, (int)gi), *Xsl = Wsl + 3 * slices * plane,
+                        *Ysl = Xsl + 3 * slices * plane;
+          int *eW = d_exp + 3 * kv_off[k], *eX = eW + ng, *eY = eX + ng;
+          HSG_LAUNCH(ctx, launch_radial(ng, kd, nt, ctx->d_radial, F, s));
+          for (int t = 0; t < nt; ++t) {
+            const int n = (int)ctx->atoms_of_type[t].size();
+            if (!n) continue;
+            HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, ng, kd, F + (size_t)t * ng * kRadStride,
+                                                ctx->d_atoms_by_type + ctx->atoms_by_type_start[t], n, ctx->d_pos,
+                                                ctx->d_rot, ctx->d_off, 0, ctx->types[t].dpad, W, depth, s));
+          }
+          HSG_LAUNCH(ctx, launch_slice(W, depth, depth, nullptr, slices, 3, Wsl, ldk, plane, eW, ng, s));
+          hsgen_status st2 = tapply_split(ctx, ng, 0, na, Wsl, ldk, eW, X, depth, slices, s);
+          if (st2 != HSGEN_OK) return st2;
+          HSG_LAUNCH(ctx, launch_slice(X, depth, depth, nullptr, slices, 3, Xsl, ldk, plane, eX, ng, s));
+          HSG_LAUNCH(ctx, launch_slice(W, depth, depth, ctx->d_urow, slices, 2, Ysl, ldk, plane, eY, ng, s));
+        }
+        for (int sg = 0; sg < nseg; ++sg) {
+          const size_t li = gi * nseg + sg;
+          if (!launch_nprob[li]) continue;
+          GemmParams P;
+          std::memset(&P, 0, sizeof(P));
+          P.gprob = d_prob + launch_first[li];
+          P.gmap = d_map + 2 * launch_first[li];
+          P.nprob = launch_nprob[li];
+          P.ntiles = launch_tiles[li];
+          P.s = slices;
+          P.status = ctx->d_status;
+          P.timeout_ns = (unsigned long long)ctx->opt.wait_timeout_ns;
+          HSG_LAUNCH(ctx, launch_gemm(P, s));
+        }
+      }
+      return HSGEN_OK;
+    };
+    st = body();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    s = caller;
+    if (st != HSGEN_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamEndCapture(batched)");
+    e = cudaGraphInstantiate(&ctx->batch_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->batch_exec = nullptr;
+      return cuda_err(ctx, e, "cudaGraphInstantiate(batched)");
+    }
+    ctx->batch_key = key;
+    ctx->stats.kernel_launches = ctx->launches;
+    s = caller;
+  }
+  HSG_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, s));
+  ctx->stats.slices = slices;
+  ctx->stats.precision = HSGEN_SPLIT;
+  ctx->phase_used[0] = 0;
+  ctx->phase_used[1] = 0;
+  return split_check_status(ctx, s);
 }
 
 void split_release(hsgen_ctx *ctx) {
@@ -928,6 +1214,14 @@ void split_release(hsgen_ctx *ctx) {
   if (ctx->d_tiles) cudaFree(ctx->d_tiles);
   ctx->d_tiles = nullptr;
   ctx->tiles_n = -1;
+  if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+  ctx->batch_exec = nullptr;
+  ctx->batch_key.clear();
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  ctx->capture_stream = nullptr;
+  if (ctx->ws_batch.ptr) cudaFree(ctx->ws_batch.ptr);
+  ctx->ws_batch.ptr = nullptr;
+  ctx->ws_batch.bytes = 0;
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   ctx->d_status = nullptr;
