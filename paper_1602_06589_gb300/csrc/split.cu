@@ -10,21 +10,28 @@
 //
 // Products (a5, part 2): C = P^H Q is, in real form,
 //   Re C = Pr^T Qr + Pi^T Qi,   Im C = Pr^T Qi - Pi^T Qr.
-// One tile is 128 output rows x 64 complex columns; its TMEM accumulator holds
-// [Re | Im] as 128 FP32 columns. The "r half" multiplies A = Pr with the B tile
-// [Qr | Qi], the "i half" A = Pi with [Qi | -Qr] (a negated plane is stored),
-// so both halves add into the same accumulator with M = N = 128 MMAs.
+// One tile is 128 output rows x 64 complex columns. The "r half" multiplies
+// A = Pr with the B block [Qr | Qi], the "i half" A = Pi with [Qi | -Qr] (a
+// negated plane is stored), so both halves add into the same [Re | Im] FP32
+// accumulator of 128 TMEM columns.
 // For a slice pair (p, q) the products are integers of magnitude <= 2^14; a
 // chunk of 1024 of them sums exactly in FP32 (|sum| <= 2^24). After each
 // chunk the epilogue warps move the FP32 accumulator into an int64 fixed-point
-// accumulator, also in TMEM, weighting pair (p, q) by 2^(-8(p+q-2)); pairs
+// accumulator held in registers, weighting pair (p, q) by 2^(-8(p+q-2)); pairs
 // with p + q > s + 1 are dropped (Ozaki-style truncation). After the last
 // chunk the tile is scaled by 2^(e_i + f_j - 14 - F) into FP64.
 //
-// Kernel roles (192 threads, one CTA per SM, persistent over tiles):
-//   warp 0    TMA producer (cp.async.bulk.tensor, 128B swizzle, 6 stages)
-//   warp 1    TMEM allocator and tcgen05.mma issuer
-//   warps 2-5 epilogue (TMEM lane quadrant = warp % 4)
+// Class pairs: the weight classes g = p + q are taken two at a time (g, g+1).
+// For a slice p of A, one M = 128, N = 256 MMA multiplies it with the B blocks
+// of q = g - p and q' = g + 1 - p side by side, into a 256-column accumulator
+// [class g | class g+1]; where only one of the two pairs exists the MMA has
+// N = 128. An N = 256 MMA does twice the work of an N = 128 one per issue,
+// which keeps the tensor core busy where 128 x 128 MMAs are issue-bound.
+//
+// Kernel roles (320 threads, one CTA per SM, persistent over tiles):
+//   warp 0     TMA producer (cp.async.bulk.tensor, 128B swizzle, 4 stages)
+//   warp 1     TMEM allocator and tcgen05.mma issuer
+//   warps 2-9  epilogue (TMEM lane quadrant = warp % 4, real or imaginary half)
 // Every wait is bounded (wait_timeout_ns); on expiry the kernel records an
 // error word, drains its own copies and MMAs (again bounded), frees TMEM and
 // returns, and the host reports HSGEN_ETIMEOUT.
@@ -45,14 +52,16 @@ namespace {
 
 constexpr int kMaxProb = 4;
 constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int NST = 7;
-constexpr int STAGE_BYTES = 32768;      // A 128x64 bf16 (16 KB) + B 128x64 bf16 (16 KB)
+constexpr int NST = 4;
+constexpr int A_BYTES = 16384;          // A 128x64 bf16
+constexpr int STAGE_BYTES = 49152;      // A (16 KB) + B 256x64 bf16 (32 KB): two slices x [re | im] blocks
 constexpr int NTHREADS = 320;           // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
-constexpr int NACC = 4;                 // FP32 accumulator buffers of 128 TMEM columns
-constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 230656 <= 232448 (227 KiB)
+constexpr int NACC = 2;                 // FP32 accumulator buffers of 256 TMEM columns
+constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 197888 <= 232448 (227 KiB)
 constexpr uint32_t TMEM_COLS = 512;
-// tcgen05 kind::f16 instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// tcgen05 kind::f16 instruction descriptors: D f32, A bf16, B bf16, both K-major, M = 128, N = 256 or 128.
+constexpr uint32_t IDESC_N256 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t IDESC_N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPILOGUE = 4 };
 
@@ -145,10 +154,10 @@ __device__ __forceinline__ void tc_relinquish() {
 __device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d), "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
@@ -264,9 +273,10 @@ __device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
 }
 
 // The accumulation schedule of one tile, identical in every role: chunk kc
-// covers complex k-blocks [kc*ckb, min(nkb, (kc+1)*ckb)); within it, slice
-// pairs (p, g-p) go by increasing weight class g = p + q <= s + 1, and up to
-// `ppc` pairs of one class share a chunk when their products still fit the
+// covers complex k-blocks [kc*ckb, min(nkb, (kc+1)*ckb)); within it the class
+// pairs (g, g+1), g = 2, 4, ... <= s + 1, go in order, and within a class pair
+// the units p = 1 .. units(g) (slice p of A times slices g - p and g + 1 - p of
+// B). Up to `ppc` units share a chunk when their products still fit the
 // 1024-product exactness bound (short depths, e.g. X = T W).
 struct Sched {
   int s, nkb, ckb, nkc, halves, ppc;
@@ -278,6 +288,10 @@ struct Sched {
     const int per_pair = (nkb < ckb ? nkb : ckb) * BK * halves;  // products per output and pair
     ppc = (nkc == 1) ? max(1, 1024 / per_pair) : 1;
   }
+  // units of the class pair based at g
+  __device__ __forceinline__ int units(int g) const { return (g + 1 <= s + 1) ? g : s; }
+  // which accumulator halves unit p of class pair g writes: bit 0 class g, bit 1 class g + 1
+  __device__ __forceinline__ int mask(int g, int p) const { return (g + 1 > s + 1) ? 1 : (p < g ? 3 : 2); }
 };
 
 // ---------------------------------------------------------------------------
@@ -330,12 +344,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
       const CUtensorMap *mA = map_a(P, ti.prob), *mB = map_b(P, ti.prob);
       for (int kc = 0; kc < sc.nkc && ok; ++kc) {
         const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
-        for (int g = 2; g <= S + 1 && ok; ++g) {
-          const int plo = max(1, g - S), phi = min(S, g - 1);
-          for (int pb = plo; pb <= phi && ok; pb += sc.ppc) {
-            const int pe = min(phi, pb + sc.ppc - 1);
+        for (int g = 2; g <= S + 1 && ok; g += 2) {
+          const int nu = sc.units(g);
+          for (int pb = 1; pb <= nu && ok; pb += sc.ppc) {
+            const int pe = min(nu, pb + sc.ppc - 1);
             for (int p = pb; p <= pe && ok; ++p) {
-              const int q = g - p;
+              const int m = sc.mask(g, p);
+              const int q0 = g - p, q1 = g + 1 - p;  // B slices of the two classes
+              const uint32_t bytes = A_BYTES + (m == 3 ? 32768u : 16384u);
               for (int kb = kb0; kb < kb1 && ok; ++kb)
                 for (int h = 0; h < sc.halves; ++h, ++it) {
                   const int st = it % NST;
@@ -345,17 +361,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
                     ok = false;
                     break;
                   }
-                  const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + 16384;
+                  const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + A_BYTES;
                   const int pa = (p - 1) * pr.a_pps + h;
-                  const int pb0 = (q - 1) * pr.b_pps + h;      // h=0: re, h=1: im
-                  const int pb1 = (q - 1) * pr.b_pps + h + 1;  // h=0: im, h=1: -re
                   const int kbA = pr.kb_begin + kb;
                   const int kbB = pr.kb_begin + ti.b_k0 / BK + kb;  // b_k0 is a multiple of 64
                   if (elect_one()) {
-                    mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
+                    mbar_expect_tx(full0 + 8 * st, bytes);
                     tma_load_3d(sA, mA, full0 + 8 * st, 0, ti.m0, pa * pr.a_nkb + kbA);
-                    tma_load_3d(sB, mB, full0 + 8 * st, 0, ti.n0, pb0 * pr.b_nkb + kbB);
-                    tma_load_3d(sB + 8192, mB, full0 + 8 * st, 0, ti.n0, pb1 * pr.b_nkb + kbB);
+                    // B rows [0, 128): class g, rows [128, 256): class g + 1; each is
+                    // [plane h | plane h + 1] = [re | im] (h = 0) or [im | -re] (h = 1)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                      if (!((m >> c) & 1)) continue;
+                      const int pq = ((c ? q1 : q0) - 1) * pr.b_pps + h;
+                      tma_load_3d(sB + c * 16384, mB, full0 + 8 * st, 0, ti.n0, pq * pr.b_nkb + kbB);
+                      tma_load_3d(sB + c * 16384 + 8192, mB, full0 + 8 * st, 0, ti.n0, (pq + 1) * pr.b_nkb + kbB);
+                    }
                   }
                   __syncwarp();
                 }
@@ -373,7 +394,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer --------------------------------
-    const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + 16384);
+    const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + A_BYTES);
     uint32_t it = 0, cc = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
@@ -382,10 +403,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
       const Sched sc(pr, ti, S);
       for (int kc = 0; kc < sc.nkc && ok; ++kc) {
         const int kb0 = kc * sc.ckb, kb1 = min(sc.nkb, kb0 + sc.ckb);
-        for (int g = 2; g <= S + 1 && ok; ++g) {
-          const int plo = max(1, g - S), phi = min(S, g - 1);
-          for (int pb = plo; pb <= phi && ok; pb += sc.ppc, ++cc) {
-            const int pe = min(phi, pb + sc.ppc - 1);
+        for (int g = 2; g <= S + 1 && ok; g += 2) {
+          const int nu = sc.units(g);
+          for (int pb = 1; pb <= nu && ok; pb += sc.ppc, ++cc) {
+            const int pe = min(nu, pb + sc.ppc - 1);
             const int buf = cc % NACC;
             const uint32_t use = cc / NACC;
             if (!warp_wait(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
@@ -394,9 +415,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
               break;
             }
             tc_fence_after();
-            const uint32_t dacc = tbase + buf * 128;
+            // the chunk's first unit writes every accumulator half the chunk uses
+            // (units with both classes come before the single-class unit p = g)
             uint32_t accum = 0;
-            for (int p = pb; p <= pe && ok; ++p)
+            for (int p = pb; p <= pe && ok; ++p) {
+              const int m = sc.mask(g, p);
+              const uint32_t idesc = (m == 3) ? IDESC_N256 : IDESC_N128;
+              const uint32_t dacc = tbase + buf * 256 + (m == 2 ? 128 : 0);
+              const uint64_t boff = (m == 2) ? (uint64_t)(16384 >> 4) : 0;
               for (int kb = kb0; kb < kb1 && ok; ++kb)
                 for (int h = 0; h < sc.halves; ++h, ++it) {
                   const int st = it % NST;
@@ -407,15 +433,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
                   }
                   tc_fence_after();
                   const uint64_t da = descA0 + (uint64_t)(st * (STAGE_BYTES >> 4));
-                  const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4));
+                  const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4)) + boff;
                   if (elect_one()) {
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) tc_mma(dacc, da + 2 * kk, db + 2 * kk, (accum | kk) ? 1u : 0u);
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                      tc_mma(dacc, da + 2 * kk, db + 2 * kk, idesc, (accum | kk) ? 1u : 0u);
                     tc_commit(empty0 + 8 * st);
                   }
                   __syncwarp();
                   accum = 1;
                 }
+            }
             if (ok) {
               if (elect_one()) tc_commit(accf0 + 8 * buf);
               __syncwarp();
@@ -448,9 +476,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
 #pragma unroll
       for (int u = 0; u < 64; ++u) acc[u] = 0;
       for (int kc = 0; kc < sc.nkc && ok; ++kc)
-        for (int g = 2; g <= S + 1 && ok; ++g) {
-          const int plo = max(1, g - S), phi = min(S, g - 1);
-          for (int pb = plo; pb <= phi && ok; pb += sc.ppc, ++cc) {
+        for (int g = 2; g <= S + 1 && ok; g += 2) {
+          const int nu = sc.units(g);
+          for (int pb = 1; pb <= nu && ok; pb += sc.ppc, ++cc) {
             const int buf = cc % NACC;
             const uint32_t use = cc / NACC;
             // one lane waits, the whole warp follows its verdict (the TMEM loads
@@ -464,18 +492,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
               break;
             }
             tc_fence_after();
-            const int sh = pr.F - 8 * (g - 2);
-            const int ish = sh > 0 ? sh : 0;
-            const float fsc = (sh < 0) ? __int_as_float((127 + sh) << 23) : 1.0f;
-            const uint32_t tacc = tbase + lane_off + buf * 128 + hf * 64;
-            uint32_t v[32];
+            const int m = sc.mask(g, pb);  // accumulator halves written in this chunk
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              tc_ld32(tacc + half * 32, v);
-              tc_wait_ld();
+            for (int c = 0; c < 2; ++c) {
+              if (!((m >> c) & 1)) continue;
+              const int sh = pr.F - 8 * (g + c - 2);
+              const int ish = sh > 0 ? sh : 0;
+              const float fsc = (sh < 0) ? __int_as_float((127 + sh) << 23) : 1.0f;
+              const uint32_t tacc = tbase + lane_off + buf * 256 + c * 128 + hf * 64;
+              uint32_t v[32];
 #pragma unroll
-              for (int u = 0; u < 32; ++u)
-                acc[half * 32 + u] += (long long)__float2int_rn(__uint_as_float(v[u]) * fsc) << ish;
+              for (int half = 0; half < 2; ++half) {
+                tc_ld32(tacc + half * 32, v);
+                tc_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 32; ++u)
+                  acc[half * 32 + u] += (long long)__float2int_rn(__uint_as_float(v[u]) * fsc) << ish;
+              }
             }
             tc_fence_before();
             __syncwarp();
