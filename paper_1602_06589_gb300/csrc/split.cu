@@ -206,11 +206,23 @@ __device__ __forceinline__ bool elect_one() {
                : "=r"(pred));
   return pred != 0;
 }
-// Bounded wait with a warp-uniform verdict (lane 0 waits, the warp follows).
+// Bounded wait of a whole converged warp with a warp-uniform verdict: every
+// lane polls the barrier (try_wait with a suspend-time hint) until the phase
+// completes or the global-timer deadline passes.
 __device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, unsigned long long timeout_ns) {
-  int got = 0;
-  if ((threadIdx.x & 31) == 0) got = mbar_wait(a, parity, timeout_ns) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, got, 0) != 0;
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred P1;\n .reg .u64 t, dl;\n"
+      " mov.u64 t, %%globaltimer;\n add.u64 dl, t, %3;\n"
+      "WARP_WAIT_LOOP:\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, 1000000;\n"
+      " @P1 bra WARP_WAIT_DONE;\n"
+      " mov.u64 t, %%globaltimer;\n setp.lt.u64 P1, t, dl;\n @P1 bra WARP_WAIT_LOOP;\n"
+      "WARP_WAIT_DONE:\n selp.u32 %0, 1, 0, P1;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity), "l"(timeout_ns)
+      : "memory");
+  return __all_sync(0xffffffffu, ok) != 0;
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 B.
