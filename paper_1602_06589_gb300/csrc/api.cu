@@ -175,9 +175,9 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
     int n1 = ty.lmax + 1;
     sp.lmax = ty.lmax;
     sp.nl = n1 * n1;
-    // depth block of one atom: 8-row aligned (16-byte TMA rule), 64-row aligned
-    // in the split form so that every k-block of the BF16 slices is whole
-    sp.dpad = round_up(2 * sp.nl, ctx->opt.precision == HSGEN_SPLIT ? 64 : 8);
+    // depth block of one atom: 8-row aligned in both forms (the split form's
+    // X = T W reads whole 64-deep blocks through depth-shifted copies of T)
+    sp.dpad = round_up(2 * sp.nl, 8);
     sp.rmt = ty.rmt;
     sp.u.assign(ty.u, ty.u + n1);
     sp.du.assign(ty.du, ty.du + n1);

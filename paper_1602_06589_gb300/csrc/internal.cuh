@@ -25,9 +25,14 @@ struct Species {
   std::vector<double> I[4];        // uu, uud, udu, udud
   std::vector<double> T_override;  // empty or (2N_L)^2 complex (interleaved), col-major
   double *d_T = nullptr;           // dpad x dpad complex col-major (ld = dpad)
-  // split form: BF16 slices of T (planes re, im per slice) and column exponents
+  // split form: BF16 slices of T (planes re, im per slice) and column exponents.
+  // T is stored once per depth shift d = 0, 8, .., 56 (kTShifts copies), each
+  // t_kspan deep with T's rows at [d, d + dpad) and zeros elsewhere, so that
+  // X = T W of an atom whose depth offset is d mod 64 reads whole 64-deep
+  // blocks of W.
   void *d_Tsl = nullptr;
   int *d_Texp = nullptr;
+  int t_kspan = 0;
   int t_real = 0;                  // imaginary part of T identically zero
 };
 

@@ -51,6 +51,7 @@ namespace hsg {
 namespace {
 
 constexpr int kMaxProb = 4;
+constexpr int kTShifts = 8;  // depth shifts 0, 8, .., 56 of the per-atom T copies
 constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int NST = 4;
 constexpr int A_BYTES = 16384;          // A 128x64 bf16
@@ -81,6 +82,7 @@ struct GemmProblem {
   const int *off;           // depth offset of each atom
   int row_base;             // depth offset of the chunk
   int n_batch, nbm, nbn;    // batch items, row blocks, column blocks
+  int a_shift_planes;       // batch mode: A planes per depth shift (the shifted copies of T)
   const int2 *tile_list;    // triangle mode: (row block, column block) of every tile, L2-friendly order
   long long tile_begin;     // first global tile index of this problem
 };
@@ -240,7 +242,7 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 // Tile schedule (identical in every role)
 // ---------------------------------------------------------------------------
 struct Tile {
-  int prob, m0, n0, b_k0, c_row0, nkb;
+  int prob, m0, n0, b_k0, c_row0, nkb, a_p0;
 };
 
 __device__ __forceinline__ const GemmProblem &problem(const GemmParams &P, int i) {
@@ -274,11 +276,14 @@ __device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
     int rem = (int)(lt % per);
     bi = rem % pr.nbm;
     bj = rem / pr.nbm;
-    koff = pr.off[pr.atoms[b]] - pr.row_base;
+    koff = pr.off[pr.atoms[b]] - pr.row_base;  // a multiple of 8
   }
   ti.m0 = bi * BM;
   ti.n0 = bj * BN;
-  ti.b_k0 = koff;
+  // B starts at the 64-deep block holding the atom's first row; A is the copy
+  // of T shifted down by the rest (zero rows elsewhere)
+  ti.b_k0 = koff & ~(BK - 1);
+  ti.a_p0 = ((koff & (BK - 1)) >> 3) * pr.a_shift_planes;
   ti.c_row0 = koff;
   ti.nkb = (pr.K + BK - 1) / BK;
   return ti;
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
                     break;
                   }
                   const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + A_BYTES;
-                  const int pa = (p - 1) * pr.a_pps + h;
+                  const int pa = ti.a_p0 + (p - 1) * pr.a_pps + h;
                   const int kbA = pr.kb_begin + kb;
                   const int kbB = pr.kb_begin + ti.b_k0 / BK + kb;  // b_k0 is a multiple of 64
                   if (elect_one()) {
@@ -801,14 +806,14 @@ hsgen_status tapply_split(hsgen_ctx *ctx, int n_g, int a0, int a1, const __nv_bf
       GemmProblem &pr = P.prob[np];
       pr.M = sp.dpad;
       pr.N = n_g;
-      pr.K = sp.dpad;
+      pr.K = sp.t_kspan;
       pr.kb_begin = 0;
       pr.a_pps = 2;
       pr.b_pps = 3;
       pr.a_real = sp.t_real;
       pr.uplo = 0;
       pr.accumulate = 0;
-      pr.F = fixed_point_bits(sp.dpad);
+      pr.F = fixed_point_bits(sp.t_kspan);
       pr.expA = sp.d_Texp;
       pr.expB = expW;
       pr.C = X;
@@ -822,9 +827,10 @@ hsgen_status tapply_split(hsgen_ctx *ctx, int n_g, int a0, int a1, const __nv_bf
       pr.tile_list = nullptr;
       pr.tile_begin = tiles;
       tiles += (long long)pr.n_batch * pr.nbm * pr.nbn;
-      pr.a_nkb = sp.dpad / BK;
+      pr.a_nkb = sp.t_kspan / BK;
       pr.b_nkb = (int)(ldk / BK);
-      if (!make_map(&P.mapA[np], sp.d_Tsl, pr.a_nkb, sp.dpad, 2LL * slices, BM) ||
+      pr.a_shift_planes = 2 * slices;
+      if (!make_map(&P.mapA[np], sp.d_Tsl, pr.a_nkb, sp.dpad, 2LL * slices * kTShifts, BM) ||
           !make_map(&P.mapB[np], Wsl, pr.b_nkb, n_g, 3LL * slices, BN))
         return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (T-apply)");
     }
@@ -900,11 +906,24 @@ hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
     if (sp.d_Texp) cudaFree(sp.d_Texp);
     sp.d_Tsl = nullptr;
     sp.d_Texp = nullptr;
-    size_t plane = (size_t)sp.dpad * sp.dpad;
-    HSG_CUDA(ctx, cudaMalloc(&sp.d_Tsl, plane * 2 * slices * sizeof(__nv_bfloat16)));
+    // shifted copies of T (FP64, kspan x dpad each), then their slices
+    sp.t_kspan = round_up(sp.dpad + BK - 8, BK);
+    const size_t span = (size_t)sp.t_kspan * sp.dpad;
+    double2 *Tsh = nullptr;
+    HSG_CUDA(ctx, cudaMalloc(&Tsh, sizeof(double2) * span * kTShifts));
+    HSG_CUDA(ctx, cudaMemset(Tsh, 0, sizeof(double2) * span * kTShifts));
+    for (int d = 0; d < kTShifts; ++d)
+      HSG_CUDA(ctx, cudaMemcpy2D(Tsh + d * span + 8 * d, sizeof(double2) * sp.t_kspan, sp.d_T,
+                                 sizeof(double2) * sp.dpad, sizeof(double2) * sp.dpad, sp.dpad,
+                                 cudaMemcpyDeviceToDevice));
+    HSG_CUDA(ctx, cudaMalloc(&sp.d_Tsl, span * 2 * slices * kTShifts * sizeof(__nv_bfloat16)));
     HSG_CUDA(ctx, cudaMalloc(&sp.d_Texp, sizeof(int) * sp.dpad));
-    HSG_CUDA(ctx, launch_slice((const double2 *)sp.d_T, sp.dpad, sp.dpad, nullptr, slices, 2,
-                               (__nv_bfloat16 *)sp.d_Tsl, sp.dpad, (long long)plane, sp.d_Texp, sp.dpad, 0));
+    for (int d = 0; d < kTShifts; ++d)
+      HSG_CUDA(ctx, launch_slice(Tsh + d * span, sp.t_kspan, sp.t_kspan, nullptr, slices, 2,
+                                 (__nv_bfloat16 *)sp.d_Tsl + d * span * 2 * slices, sp.t_kspan, (long long)span,
+                                 sp.d_Texp, sp.dpad, 0));
+    HSG_CUDA(ctx, cudaDeviceSynchronize());
+    cudaFree(Tsh);
     // does T have an imaginary part?
     std::vector<double2> h((size_t)sp.dpad * sp.dpad);
     HSG_CUDA(ctx, cudaMemcpy(h.data(), sp.d_T, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost));
