@@ -28,9 +28,17 @@
 // N = 128. An N = 256 MMA does twice the work of an N = 128 one per issue,
 // which keeps the tensor core busy where 128 x 128 MMAs are issue-bound.
 //
-// Kernel roles (320 threads, one CTA per SM, persistent over tiles):
-//   warp 0     TMA producer (cp.async.bulk.tensor, 128B swizzle, 4 stages)
-//   warp 1     TMEM allocator and tcgen05.mma issuer
+// CTA pairs: a tile is 256 output rows x 64 complex columns, computed by two
+// CTAs (a cluster of 2 on two SMs) with M = 256 tcgen05 MMAs of cta_group::2.
+// Each CTA loads its own 128 rows of A and its half of B (the class-g block in
+// CTA 0, the class-(g+1) block in CTA 1), so an SM takes in 32 KB of operands
+// per 64-deep step instead of 48 KB; the leader CTA issues the MMAs, which
+// read both CTAs' shared memory and write each CTA's 128 rows into its own
+// tensor memory.
+//
+// Kernel roles (320 threads per CTA, one CTA per SM, persistent over tiles):
+//   warp 0     TMA producer (cp.async.bulk.tensor, 128B swizzle, 7 stages)
+//   warp 1     TMEM allocator; tcgen05.mma issuer in the leader CTA
 //   warps 2-9  epilogue (TMEM lane quadrant = warp % 4, real or imaginary half)
 // Every wait is bounded (wait_timeout_ns); on expiry the kernel records an
 // error word, drains its own copies and MMAs (again bounded), frees TMEM and
@@ -52,17 +60,18 @@ namespace {
 
 constexpr int kMaxProb = 4;
 constexpr int kTShifts = 8;  // depth shifts 0, 8, .., 56 of the per-atom T copies
-constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int NST = 4;
-constexpr int A_BYTES = 16384;          // A 128x64 bf16
-constexpr int STAGE_BYTES = 49152;      // A (16 KB) + B 256x64 bf16 (32 KB): two slices x [re | im] blocks
+// BM: rows of A per CTA (one TMA box); BMT: rows of a tile (a CTA pair)
+constexpr int BM = 128, BMT = 256, BN = 64, BK = 64;
+constexpr int NST = 7;
+constexpr int A_BYTES = 16384;          // A 128x64 bf16 (this CTA's rows)
+constexpr int STAGE_BYTES = 32768;      // A (16 KB) + this CTA's half of B (128x64 bf16, 16 KB)
 constexpr int NTHREADS = 320;           // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int NACC = 2;                 // FP32 accumulator buffers of 256 TMEM columns
-constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 197888 <= 232448 (227 KiB)
+constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 230656 <= 232448 (227 KiB)
 constexpr uint32_t TMEM_COLS = 512;
-// tcgen05 kind::f16 instruction descriptors: D f32, A bf16, B bf16, both K-major, M = 128, N = 256 or 128.
-constexpr uint32_t IDESC_N256 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t IDESC_N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// tcgen05 kind::f16 instruction descriptors: D f32, A bf16, B bf16, both K-major, M = 256 (CTA pair), N = 256 or 128.
+constexpr uint32_t IDESC_N256 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
+constexpr uint32_t IDESC_N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
 
 enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPILOGUE = 4 };
 
@@ -117,9 +126,6 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t n) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -140,43 +146,62 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, unsigned 
     if (gtime() - t0 > timeout_ns) return false;
   }
 }
+// Both CTAs of a pair load into their own shared memory and signal the
+// leader CTA's barrier (`mbar` is a shared::cluster address).
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t mbar, int c0, int c1,
                                             int c2) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];"
       ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
+__device__ __forceinline__ uint32_t cta_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Tensor memory of a CTA pair: one warp of each CTA takes part in allocation,
+// permit release and deallocation; the leader CTA issues the MMAs, which read
+// A and B from both CTAs' shared memory and write both CTAs' tensor memory.
 __device__ __forceinline__ void tc_alloc(uint32_t dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
 }
 __device__ __forceinline__ void tc_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// arrives on the barrier at offset `mbar` in both CTAs of the pair once the
+// MMAs issued so far have completed
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(mbar), "h"((uint16_t)3)
+               : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -186,16 +211,6 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-}
-__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
-      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
-        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
-        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]), "r"(r[32])
-      : "memory");
 }
 
 // One lane of the (converged) warp; the warp's other lanes skip the guarded
@@ -211,19 +226,34 @@ __device__ __forceinline__ bool elect_one() {
 // Bounded wait of a whole converged warp with a warp-uniform verdict: every
 // lane polls the barrier (try_wait with a suspend-time hint) until the phase
 // completes or the global-timer deadline passes.
+// `Cluster`: acquire at cluster scope (arrivals released by the peer CTA).
+template <bool Cluster = false>
 __device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, unsigned long long timeout_ns) {
   uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred P1;\n .reg .u64 t, dl;\n"
-      " mov.u64 t, %%globaltimer;\n add.u64 dl, t, %3;\n"
-      "WARP_WAIT_LOOP:\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, 1000000;\n"
-      " @P1 bra WARP_WAIT_DONE;\n"
-      " mov.u64 t, %%globaltimer;\n setp.lt.u64 P1, t, dl;\n @P1 bra WARP_WAIT_LOOP;\n"
-      "WARP_WAIT_DONE:\n selp.u32 %0, 1, 0, P1;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity), "l"(timeout_ns)
-      : "memory");
+  if (Cluster)
+    asm volatile(
+        "{\n .reg .pred P1;\n .reg .u64 t, dl;\n"
+        " mov.u64 t, %%globaltimer;\n add.u64 dl, t, %3;\n"
+        "WARP_WAIT_LOOP:\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 P1, [%1], %2, 1000000;\n"
+        " @P1 bra WARP_WAIT_DONE;\n"
+        " mov.u64 t, %%globaltimer;\n setp.lt.u64 P1, t, dl;\n @P1 bra WARP_WAIT_LOOP;\n"
+        "WARP_WAIT_DONE:\n selp.u32 %0, 1, 0, P1;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "l"(timeout_ns)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred P1;\n .reg .u64 t, dl;\n"
+        " mov.u64 t, %%globaltimer;\n add.u64 dl, t, %3;\n"
+        "WARP_WAIT_LOOP:\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, 1000000;\n"
+        " @P1 bra WARP_WAIT_DONE;\n"
+        " mov.u64 t, %%globaltimer;\n setp.lt.u64 P1, t, dl;\n @P1 bra WARP_WAIT_LOOP;\n"
+        "WARP_WAIT_DONE:\n selp.u32 %0, 1, 0, P1;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "l"(timeout_ns)
+        : "memory");
   return __all_sync(0xffffffffu, ok) != 0;
 }
 
@@ -278,7 +308,7 @@ __device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
     bj = rem / pr.nbm;
     koff = pr.off[pr.atoms[b]] - pr.row_base;  // a multiple of 8
   }
-  ti.m0 = bi * BM;
+  ti.m0 = bi * BMT;
   ti.n0 = bj * BN;
   // B starts at the 64-deep block holding the atom's first row; A is the copy
   // of T shifted down by the rest (zero rows elsewhere)
@@ -314,7 +344,8 @@ struct Sched {
 // ---------------------------------------------------------------------------
 // The persistent split GEMM kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_constant__ GemmParams P) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    split_gemm_kernel(const __grid_constant__ GemmParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES);
@@ -324,6 +355,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
                  acce0 = accf0 + 8 * NACC, tdown = acce0 + 8 * NACC;
   const uint32_t sbase = smem_u32(smem);
   const unsigned long long tmo = P.timeout_ns;
+  // CTA pair: rank 0 (leader) issues the MMAs; its `full` barriers count both
+  // CTAs' copies and its `acce` barriers both CTAs' epilogue warps
+  const uint32_t rank = cta_rank();
+  const bool leader = rank == 0;
+  const uint32_t lead_full0 = map_rank(full0, 0), lead_acce0 = map_rank(acce0, 0);
+  const long long pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NST; ++i) {
@@ -332,7 +369,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     }
     for (int i = 0; i < NACC; ++i) {
       mbar_init(accf0 + 8 * i, 1);
-      mbar_init(acce0 + 8 * i, 8);  // one arrival per epilogue warp
+      mbar_init(acce0 + 8 * i, 16);  // one arrival per epilogue warp of either CTA
     }
     mbar_init(tdown, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -344,6 +381,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // both CTAs' barriers exist before either signals the other's
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
   const int S = P.s;
@@ -354,7 +392,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     // ------------------------------ TMA producer ------------------------------
     uint32_t it = 0;
     bool ok = true;
-    for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+    for (long long t = pair; t < P.ntiles && ok; t += npairs) {
       const Tile ti = decode_tile(P, t);
       const GemmProblem &pr = problem(P, ti.prob);
       const Sched sc(pr, ti, S);
@@ -368,7 +406,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
             for (int p = pb; p <= pe && ok; ++p) {
               const int m = sc.mask(g, p);
               const int q0 = g - p, q1 = g + 1 - p;  // B slices of the two classes
-              const uint32_t bytes = A_BYTES + (m == 3 ? 32768u : 16384u);
+              // both CTAs' bytes, expected on the leader's barrier
+              const uint32_t bytes = 2 * A_BYTES + (m == 3 ? 32768u : 16384u);
               for (int kb = kb0; kb < kb1 && ok; ++kb)
                 for (int h = 0; h < sc.halves; ++h, ++it) {
                   const int st = it % NST;
@@ -379,20 +418,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
                     break;
                   }
                   const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + A_BYTES;
+                  const uint32_t mbar = lead_full0 + 8 * st;
                   const int pa = ti.a_p0 + (p - 1) * pr.a_pps + h;
                   const int kbA = pr.kb_begin + kb;
                   const int kbB = pr.kb_begin + ti.b_k0 / BK + kb;  // b_k0 is a multiple of 64
                   if (elect_one()) {
-                    mbar_expect_tx(full0 + 8 * st, bytes);
-                    tma_load_3d(sA, mA, full0 + 8 * st, 0, ti.m0, pa * pr.a_nkb + kbA);
-                    // B rows [0, 128): class g, rows [128, 256): class g + 1; each is
-                    // [plane h | plane h + 1] = [re | im] (h = 0) or [im | -re] (h = 1)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                      if (!((m >> c) & 1)) continue;
-                      const int pq = ((c ? q1 : q0) - 1) * pr.b_pps + h;
-                      tma_load_3d(sB + c * 16384, mB, full0 + 8 * st, 0, ti.n0, pq * pr.b_nkb + kbB);
-                      tma_load_3d(sB + c * 16384 + 8192, mB, full0 + 8 * st, 0, ti.n0, (pq + 1) * pr.b_nkb + kbB);
+                    if (leader) mbar_expect_tx(full0 + 8 * st, bytes);
+                    tma_load_3d(sA, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA);
+                    // The pair's B operand is split by rows between the CTAs. N = 256:
+                    // rows [0, 128) class g (CTA 0), [128, 256) class g + 1 (CTA 1), each
+                    // [plane h | plane h + 1] = [re | im] (h = 0) or [im | -re] (h = 1).
+                    // N = 128 (one class): plane h in CTA 0, plane h + 1 in CTA 1.
+                    if (m == 3) {
+                      const int pq = ((rank ? q1 : q0) - 1) * pr.b_pps + h;
+                      tma_load_3d(sB, mB, mbar, 0, ti.n0, pq * pr.b_nkb + kbB);
+                      tma_load_3d(sB + 8192, mB, mbar, 0, ti.n0, (pq + 1) * pr.b_nkb + kbB);
+                    } else {
+                      const int pq = ((m == 1 ? q0 : q1) - 1) * pr.b_pps + h + (int)rank;
+                      tma_load_3d(sB, mB, mbar, 0, ti.n0, pq * pr.b_nkb + kbB);
                     }
                   }
                   __syncwarp();
@@ -403,18 +446,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
       }
     }
     // no copy may still be in flight at teardown: the latest use of every
-    // stage must have landed (bounded)
-    for (int st = 0; st < NST; ++st) {
+    // stage must have landed in both CTAs (bounded; the leader's barriers
+    // count both, and the final cluster barrier holds the peer until then)
+    for (int st = 0; st < NST && leader; ++st) {
       if (it <= (uint32_t)st) break;
       const uint32_t j = st + NST * ((it - 1 - st) / NST);
       if (!warp_wait(full0 + 8 * st, (j / NST) & 1, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 && leader) {
     // ------------------------------ MMA issuer --------------------------------
     const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + A_BYTES);
     uint32_t it = 0, cc = 0;
     bool ok = true;
-    for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+    for (long long t = pair; t < P.ntiles && ok; t += npairs) {
       const Tile ti = decode_tile(P, t);
       const GemmProblem &pr = problem(P, ti.prob);
       const Sched sc(pr, ti, S);
@@ -426,7 +470,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
             const int pe = min(nu, pb + sc.ppc - 1);
             const int buf = cc % NACC;
             const uint32_t use = cc / NACC;
-            if (!warp_wait(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
+            if (!warp_wait<true>(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
               if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
               ok = false;
               break;
@@ -439,7 +483,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
               const int m = sc.mask(g, p);
               const uint32_t idesc = (m == 3) ? IDESC_N256 : IDESC_N128;
               const uint32_t dacc = tbase + buf * 256 + (m == 2 ? 128 : 0);
-              const uint64_t boff = (m == 2) ? (uint64_t)(16384 >> 4) : 0;
               for (int kb = kb0; kb < kb1 && ok; ++kb)
                 for (int h = 0; h < sc.halves; ++h, ++it) {
                   const int st = it % NST;
@@ -450,7 +493,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
                   }
                   tc_fence_after();
                   const uint64_t da = descA0 + (uint64_t)(st * (STAGE_BYTES >> 4));
-                  const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4)) + boff;
+                  const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4));
                   if (elect_one()) {
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk)
@@ -473,7 +516,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     if (elect_one()) tc_commit(tdown);
     __syncwarp();
     if (!warp_wait(tdown, 0, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
-  } else {
+  } else if (warp >= 2) {
     // ------------------------------ epilogue ----------------------------------
     // Eight warps: warp w reads TMEM lane quadrant w % 4 (rows), and half hf of
     // the accumulator columns (hf 0: real parts, hf 1: imaginary parts of the
@@ -485,7 +528,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
     const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
     uint32_t cc = 0;
     bool ok = true;
-    for (long long t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+    for (long long t = pair; t < P.ntiles && ok; t += npairs) {
       const Tile ti = decode_tile(P, t);
       const GemmProblem &pr = problem(P, ti.prob);
       const Sched sc(pr, ti, S);
@@ -529,12 +572,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acce0 + 8 * buf);
+            if (lane == 0) mbar_arrive_cluster(lead_acce0 + 8 * buf);
           }
         }
       if (!ok) break;
       // ---- tile output: int64 fixed point -> FP64, scaled by 2^(eA + eB - 14 - F)
-      const int row = ti.m0 + qd * 32 + lane;  // row within the problem
+      const int row = ti.m0 + (int)rank * BM + qd * 32 + lane;  // row within the problem
       if (row < pr.M) {
         const int eA = pr.expA[row];
         const long long grow = (long long)ti.c_row0 + row;  // row in C
@@ -567,6 +610,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(const __grid_co
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // the leader's MMAs and both CTAs' copies are complete
   tc_fence_after();
   if (warp == 1) tc_dealloc(tbase, TMEM_COLS);
 }
@@ -707,6 +751,24 @@ int num_sms() {
   return n;
 }
 
+// CTA pairs that can be resident at once (one pair per two SMs).
+int max_pairs() {
+  static int n = 0;
+  if (!n) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (num_sms() / 2));
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, (const void *)split_gemm_kernel, &cfg) != cudaSuccess || c <= 0) {
+      cudaGetLastError();
+      c = num_sms() / 2;
+    }
+    n = std::max(1, c);
+  }
+  return n;
+}
+
 cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
@@ -715,8 +777,8 @@ cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
     attr = true;
   }
   if (P.ntiles <= 0) return cudaSuccess;
-  long long grid = std::min<long long>(P.ntiles, num_sms());
-  split_gemm_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(P);
+  const long long pairs = std::min<long long>(P.ntiles, max_pairs());
+  split_gemm_kernel<<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
   return cudaGetLastError();
 }
 
@@ -763,13 +825,13 @@ SplitWs split_ws_layout(void *base, int n_g, int depth, int s) {
 // few A row blocks and kBand B column blocks through L2.
 std::vector<int2> tri_tiles(int n, int uplo) {
   constexpr int kBand = 16;
-  const int nbm = (n + BM - 1) / BM, nbn = (n + BN - 1) / BN;
+  const int nbm = (n + BMT - 1) / BMT, nbn = (n + BN - 1) / BN;
   std::vector<int2> out;
   for (int b0 = 0; b0 < nbn; b0 += kBand) {
     const int b1 = std::min(nbn, b0 + kBand);
     for (int bi = 0; bi < nbm; ++bi)
       for (int bj = b0; bj < b1; ++bj) {
-        const bool valid = (uplo == 'U') ? (bi * BM <= bj * BN + BN - 1) : (bi * BM + BM - 1 >= bj * BN);
+        const bool valid = (uplo == 'U') ? (bi * BMT <= bj * BN + BN - 1) : (bi * BMT + BMT - 1 >= bj * BN);
         if (valid) out.push_back(make_int2(bi, bj));
       }
   }
@@ -822,7 +884,7 @@ hsgen_status tapply_split(hsgen_ctx *ctx, int n_g, int a0, int a1, const __nv_bf
       pr.off = ctx->d_off;
       pr.row_base = row_base;
       pr.n_batch = ranges[b].second - ranges[b].first;
-      pr.nbm = (sp.dpad + BM - 1) / BM;
+      pr.nbm = (sp.dpad + BMT - 1) / BMT;
       pr.nbn = (n_g + BN - 1) / BN;
       pr.tile_list = nullptr;
       pr.tile_begin = tiles;
@@ -865,7 +927,7 @@ bool hs_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, lon
     q.C = (k == 0) ? H : S;
     q.ldc = ld;
     q.n_batch = 1;
-    q.nbm = (n_g + BM - 1) / BM;
+    q.nbm = (n_g + BMT - 1) / BMT;
     q.nbn = (n_g + BN - 1) / BN;
     q.tile_list = tiles;
     q.tile_begin = tile_begin + k * ntiles;
