@@ -32,12 +32,12 @@
 // CTAs (a cluster of 2 on two SMs) with M = 256 tcgen05 MMAs of cta_group::2.
 // Each CTA loads its own 128 rows of A and its half of B (the class-g block in
 // CTA 0, the class-(g+1) block in CTA 1), so an SM takes in 32 KB of operands
-// per 64-deep step instead of 48 KB; the leader CTA issues the MMAs, which
+// per 64-deep block instead of 48 KB; the leader CTA issues the MMAs, which
 // read both CTAs' shared memory and write each CTA's 128 rows into its own
 // tensor memory.
 //
 // Kernel roles (320 threads per CTA, one CTA per SM, persistent over tiles):
-//   warp 0     TMA producer (cp.async.bulk.tensor, 128B swizzle, 7 stages)
+//   warp 0     TMA producer (cp.async.bulk.tensor, 128B swizzle, 3 stages of 2 k-blocks)
 //   warp 1     TMEM allocator; tcgen05.mma issuer in the leader CTA
 //   warps 2-9  epilogue (TMEM lane quadrant = warp % 4, real or imaginary half)
 // Every wait is bounded (wait_timeout_ns); on expiry the kernel records an
@@ -62,12 +62,17 @@ constexpr int kMaxProb = 4;
 constexpr int kTShifts = 8;  // depth shifts 0, 8, .., 56 of the per-atom T copies
 // BM: rows of A per CTA (one TMA box); BMT: rows of a tile (a CTA pair)
 constexpr int BM = 128, BMT = 256, BN = 64, BK = 64;
-constexpr int NST = 7;
-constexpr int A_BYTES = 16384;          // A 128x64 bf16 (this CTA's rows)
-constexpr int STAGE_BYTES = 32768;      // A (16 KB) + this CTA's half of B (128x64 bf16, 16 KB)
+// A pipeline stage holds KPS 64-deep k-blocks: large stages keep the fixed
+// cost of each barrier round trip small next to the bytes moved.
+constexpr int KPS = 2;
+constexpr int NST = 3;
+constexpr int A_BYTES = 16384;                 // one k-block of A: 128x64 bf16 (this CTA's rows)
+constexpr int B_BYTES = 16384;                 // one k-block of this CTA's half of B: 128x64 bf16
+constexpr int STAGE_A = KPS * A_BYTES;         // A k-blocks of a stage, then its B k-blocks
+constexpr int STAGE_BYTES = KPS * (A_BYTES + B_BYTES);
 constexpr int NTHREADS = 320;           // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int NACC = 2;                 // FP32 accumulator buffers of 256 TMEM columns
-constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 230656 <= 232448 (227 KiB)
+constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 197888 <= 232448 (227 KiB)
 constexpr uint32_t TMEM_COLS = 512;
 // tcgen05 kind::f16 instruction descriptors: D f32, A bf16, B bf16, both K-major, M = 256 (CTA pair), N = 256 or 128.
 constexpr uint32_t IDESC_N256 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
@@ -406,9 +411,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             for (int p = pb; p <= pe && ok; ++p) {
               const int m = sc.mask(g, p);
               const int q0 = g - p, q1 = g + 1 - p;  // B slices of the two classes
-              // both CTAs' bytes, expected on the leader's barrier
-              const uint32_t bytes = 2 * A_BYTES + (m == 3 ? 32768u : 16384u);
-              for (int kb = kb0; kb < kb1 && ok; ++kb)
+              for (int kb = kb0; kb < kb1 && ok; kb += KPS) {
+                const int nk = min(KPS, kb1 - kb);
+                // both CTAs' bytes, expected on the leader's barrier
+                const uint32_t bytes = nk * (2 * A_BYTES + (m == 3 ? 2 * B_BYTES : B_BYTES));
                 for (int h = 0; h < sc.halves; ++h, ++it) {
                   const int st = it % NST;
                   const uint32_t round = it / NST;
@@ -417,29 +423,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     ok = false;
                     break;
                   }
-                  const uint32_t sA = sbase + st * STAGE_BYTES, sB = sA + A_BYTES;
+                  const uint32_t sA0 = sbase + st * STAGE_BYTES;
                   const uint32_t mbar = lead_full0 + 8 * st;
                   const int pa = ti.a_p0 + (p - 1) * pr.a_pps + h;
                   const int kbA = pr.kb_begin + kb;
                   const int kbB = pr.kb_begin + ti.b_k0 / BK + kb;  // b_k0 is a multiple of 64
                   if (elect_one()) {
                     if (leader) mbar_expect_tx(full0 + 8 * st, bytes);
-                    tma_load_3d(sA, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA);
-                    // The pair's B operand is split by rows between the CTAs. N = 256:
-                    // rows [0, 128) class g (CTA 0), [128, 256) class g + 1 (CTA 1), each
-                    // [plane h | plane h + 1] = [re | im] (h = 0) or [im | -re] (h = 1).
-                    // N = 128 (one class): plane h in CTA 0, plane h + 1 in CTA 1.
-                    if (m == 3) {
-                      const int pq = ((rank ? q1 : q0) - 1) * pr.b_pps + h;
-                      tma_load_3d(sB, mB, mbar, 0, ti.n0, pq * pr.b_nkb + kbB);
-                      tma_load_3d(sB + 8192, mB, mbar, 0, ti.n0, (pq + 1) * pr.b_nkb + kbB);
-                    } else {
-                      const int pq = ((m == 1 ? q0 : q1) - 1) * pr.b_pps + h + (int)rank;
-                      tma_load_3d(sB, mB, mbar, 0, ti.n0, pq * pr.b_nkb + kbB);
+                    for (int j = 0; j < nk; ++j) {
+                      const uint32_t sA = sA0 + j * A_BYTES, sB = sA0 + STAGE_A + j * B_BYTES;
+                      tma_load_3d(sA, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA + j);
+                      // The pair's B operand is split by rows between the CTAs. N = 256:
+                      // rows [0, 128) class g (CTA 0), [128, 256) class g + 1 (CTA 1), each
+                      // [plane h | plane h + 1] = [re | im] (h = 0) or [im | -re] (h = 1).
+                      // N = 128 (one class): plane h in CTA 0, plane h + 1 in CTA 1.
+                      if (m == 3) {
+                        const int pq = ((rank ? q1 : q0) - 1) * pr.b_pps + h;
+                        tma_load_3d(sB, mB, mbar, 0, ti.n0, pq * pr.b_nkb + kbB + j);
+                        tma_load_3d(sB + 8192, mB, mbar, 0, ti.n0, (pq + 1) * pr.b_nkb + kbB + j);
+                      } else {
+                        const int pq = ((m == 1 ? q0 : q1) - 1) * pr.b_pps + h + (int)rank;
+                        tma_load_3d(sB, mB, mbar, 0, ti.n0, pq * pr.b_nkb + kbB + j);
+                      }
                     }
                   }
                   __syncwarp();
                 }
+              }
             }
           }
         }
@@ -455,7 +465,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1 && leader) {
     // ------------------------------ MMA issuer --------------------------------
-    const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + A_BYTES);
+    const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + STAGE_A);
     uint32_t it = 0, cc = 0;
     bool ok = true;
     for (long long t = pair; t < P.ntiles && ok; t += npairs) {
@@ -483,7 +493,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
               const int m = sc.mask(g, p);
               const uint32_t idesc = (m == 3) ? IDESC_N256 : IDESC_N128;
               const uint32_t dacc = tbase + buf * 256 + (m == 2 ? 128 : 0);
-              for (int kb = kb0; kb < kb1 && ok; ++kb)
+              for (int kb = kb0; kb < kb1 && ok; kb += KPS) {
+                const int nk = min(KPS, kb1 - kb);
                 for (int h = 0; h < sc.halves; ++h, ++it) {
                   const int st = it % NST;
                   if (!warp_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
@@ -495,14 +506,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                   const uint64_t da = descA0 + (uint64_t)(st * (STAGE_BYTES >> 4));
                   const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4));
                   if (elect_one()) {
+                    for (int j = 0; j < nk; ++j) {
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)
-                      tc_mma(dacc, da + 2 * kk, db + 2 * kk, idesc, (accum | kk) ? 1u : 0u);
+                      for (int kk = 0; kk < BK / 16; ++kk)
+                        tc_mma(dacc, da + (uint64_t)(j * (A_BYTES >> 4)) + 2 * kk,
+                               db + (uint64_t)(j * (B_BYTES >> 4)) + 2 * kk, idesc, (accum | j | kk) ? 1u : 0u);
+                    }
                     tc_commit(empty0 + 8 * st);
                   }
                   __syncwarp();
                   accum = 1;
                 }
+              }
             }
             if (ok) {
               if (elect_one()) tc_commit(accf0 + 8 * buf);
