@@ -221,6 +221,173 @@ def run_batched(args, w, world, rank, local, dist):
         print(json.dumps(line), flush=True)
 
 
+def _cublas(torch):
+    """The cuBLAS library torch has loaded (the same instance, so its handle is valid)."""
+    import ctypes
+
+    a = torch.zeros((2, 2), dtype=torch.complex128, device="cuda")
+    (a @ a).sum().item()  # makes torch initialise cuBLAS
+    path = None
+    with open("/proc/self/maps") as f:
+        for line in f:
+            if "libcublas.so" in line and "libcublasLt" not in line:
+                path = line.split()[-1]
+                break
+    if path is None:
+        raise RuntimeError("libcublas is not loaded")
+    lib = ctypes.CDLL(path)
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    lib.cublasZgemm_v2.argtypes = [vp, i, i, i, i, i, vp, vp, i, vp, i, vp, vp, i]
+    lib.cublasZherk_v2.argtypes = [vp, i, i, i, i, vp, vp, i, vp, vp, i]
+    lib.cublasDgemm_v2.argtypes = [vp, i, i, i, i, i, vp, vp, i, vp, i, vp, vp, i]
+    lib.cublasSetMathMode.argtypes = [vp, i]
+    lib.cublasSetEmulationStrategy.argtypes = [vp, i]
+    return lib
+
+
+def library_bars(args, w):
+    """Library bars on the same workload, beside this library's split form:
+    (1) cuBLAS ZGEMM (H = W^H X, full) + ZHERK (S = V^H V, V = diag(sqrt(u)) W,
+    upper triangle) in plain FP64; (2) the same products in real form,
+    Re/Im H = [Wr; Wi]^T [Xr; Xi] / [Wr; Wi]^T [Xi; -Xr] and likewise for S,
+    as four DGEMMs of depth 2D, in plain FP64 and with cuBLAS's FP64
+    fixed-point emulation (EAGER strategy). Operands are built with this
+    library's coefficient and T-matrix calls; the cuBLAS calls are the library
+    under test and are timed without operand construction."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_1602_06589_gb300 import flops, hsgen
+
+    dev = torch.device("cuda", 0)
+    sysm, kv = w.system, w.kvecs[0]
+    n = kv.shape[0]
+    nls = [sysm.types[t].nl for t in sysm.type_of_atom]
+    fa = flops.algorithmic_flops(n, nls)
+    lib = _cublas(torch)
+    handle = ctypes.c_void_p(torch.cuda.current_blas_handle())
+    kvd = torch.from_numpy(kv).to(dev)
+    with hsgen.Generator(sysm, precision=hsgen.SPLIT) as g:
+        # ours: the split form, timed like the benchmark
+        H1, S1 = g.build(kvd)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ours = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            ev[0].record()
+            H1, S1 = g.build(kvd, H1.mT, S1.mT)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ours.append(ev[0].elapsed_time(ev[1]) / 1e3)
+        off = g.depth_offsets
+        Wpad = g.coefficients(kvd).mT  # (N_G, depth): row t = column t of W
+        rows, urow = [], []
+        for a, ti in enumerate(sysm.type_of_atom):
+            ty = sysm.types[ti]
+            nl = ty.nl
+            rows.append(np.arange(off[a], off[a] + 2 * nl))
+            l_of = np.repeat(np.arange(ty.lmax + 1), 2 * np.arange(ty.lmax + 1) + 1)
+            urow.append(np.concatenate([np.ones(nl), np.asarray(ty.udot_norm2)[l_of]]))
+        rows = torch.from_numpy(np.concatenate(rows)).to(dev)
+        u = torch.from_numpy(np.concatenate(urow)).to(dev)
+        Wc = Wpad[:, rows].contiguous()  # (N_G, D): column-major D x N_G, ld D
+        del Wpad
+        D = Wc.shape[1]
+        X = torch.empty_like(Wc)
+        c0 = 0
+        for a, ti in enumerate(sysm.type_of_atom):
+            m2 = 2 * sysm.types[ti].nl
+            T = torch.from_numpy(g.T_matrix(ti)).to(dev)
+            X[:, c0:c0 + m2] = Wc[:, c0:c0 + m2] @ T.mT  # X_a = T W_a
+            c0 += m2
+        V = (Wc * torch.sqrt(u)).contiguous()
+    Hc = torch.zeros((n, n), dtype=torch.complex128, device=dev)  # column-major buffers
+    Sc = torch.zeros_like(Hc)
+    one = (ctypes.c_double * 2)(1.0, 0.0)
+    zero = (ctypes.c_double * 2)(0.0, 0.0)
+    d1, d0 = ctypes.c_double(1.0), ctypes.c_double(0.0)
+
+    def run():
+        st = lib.cublasZgemm_v2(handle, 2, 0, n, n, D, ctypes.cast(one, ctypes.c_void_p), Wc.data_ptr(), D,
+                                X.data_ptr(), D, ctypes.cast(zero, ctypes.c_void_p), Hc.data_ptr(), n)
+        st2 = lib.cublasZherk_v2(handle, 1, 2, n, D, ctypes.byref(d1), V.data_ptr(), D, ctypes.byref(d0),
+                                 Sc.data_ptr(), n)
+        if st or st2:
+            raise RuntimeError(f"cuBLAS status {st} {st2}")
+
+    def timed(fn, reps):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev[0].record()
+            fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]) / 1e3)
+        return statistics.median(ts)
+
+    iu = torch.triu_indices(n, n, device=dev)
+
+    def rel(A, B):  # A, B column-major buffers, compared on the upper triangle
+        a, b = A.mT[iu[0], iu[1]], B.mT[iu[0], iu[1]]
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    t_native = timed(run, args.bar_reps)
+    Hn, Sn = Hc.clone(), Sc.clone()
+    del Hc, Sc
+    # real form: stacked (n, 2D) row-major = column-major 2D x n operands
+    Wr = torch.cat([Wc.real, Wc.imag], dim=1).contiguous()
+    Xr = torch.cat([X.real, X.imag], dim=1).contiguous()
+    Xs = torch.cat([X.imag, -X.real], dim=1).contiguous()
+    Vr = torch.cat([V.real, V.imag], dim=1).contiguous()
+    Vs = torch.cat([V.imag, -V.real], dim=1).contiguous()
+    del Wc, X, V
+    R = [torch.zeros((n, n), dtype=torch.float64, device=dev) for _ in range(4)]
+    d_one, d_zero = ctypes.c_double(1.0), ctypes.c_double(0.0)
+
+    def run_real():
+        for (A, B, C) in ((Wr, Xr, R[0]), (Wr, Xs, R[1]), (Vr, Vr, R[2]), (Vr, Vs, R[3])):
+            st = lib.cublasDgemm_v2(handle, 1, 0, n, n, 2 * D, ctypes.byref(d_one), A.data_ptr(), 2 * D,
+                                    B.data_ptr(), 2 * D, ctypes.byref(d_zero), C.data_ptr(), n)
+            if st:
+                raise RuntimeError(f"cuBLAS DGEMM status {st}")
+
+    def as_complex():
+        return torch.complex(R[0], R[1]), torch.complex(R[2], R[3])
+
+    t_real = timed(run_real, args.bar_reps)
+    Hr, Sr = as_complex()
+    err_real = (rel(Hr, Hn), rel(Sr, Sn))
+    del Hr, Sr
+    lib.cublasSetMathMode(handle, 8)  # CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
+    lib.cublasSetEmulationStrategy(handle, 2)  # CUBLAS_EMULATION_STRATEGY_EAGER
+    try:
+        t_emul = timed(run_real, args.bar_reps)
+    finally:
+        lib.cublasSetMathMode(handle, 0)
+        lib.cublasSetEmulationStrategy(handle, 0)
+    He, Se = as_complex()
+    err_emul = (rel(He, Hn), rel(Se, Sn))
+    F = fa["total"]
+    out = {
+        "metric": METRIC, "impl": "library-bars", "unit": "s/k-point",
+        "config": {"workload": workload_name(args.config, w), "depth": D},
+        "ours_split": {"s": statistics.median(ours), "eff_tflops": F / statistics.median(ours) / 1e12,
+                       "rel_err_H_vs_cublas_fp64": rel(H1.mT, Hn), "rel_err_S_vs_cublas_fp64": rel(S1.mT, Sn)},
+        "cublas_fp64": {"s": t_native, "eff_tflops": F / t_native / 1e12, "calls": "ZGEMM (H, full) + ZHERK (S)"},
+        "cublas_fp64_real_form": {"s": t_real, "eff_tflops": F / t_real / 1e12, "calls": "4 DGEMM, depth 2D",
+                                  "rel_err_H": err_real[0], "rel_err_S": err_real[1]},
+        "cublas_fp64_emulated": {"s": t_emul, "eff_tflops": F / t_emul / 1e12, "calls": "4 DGEMM, depth 2D",
+                                 "rel_err_H": err_emul[0], "rel_err_S": err_emul[1],
+                                 "mode": "CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH, EAGER"},
+        "note": "H + S only (operands pre-built, not timed) for cuBLAS; ours includes coefficients and T-apply",
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -232,10 +399,13 @@ def main():
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-columns", type=int, default=48)
+    ap.add_argument("--ref-columns", type=int, default=384)
     ap.add_argument("--n-g", type=int, default=0, help="override N_G (smaller cases for profiling)")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="also time one FP64-form step on the same workload")
+    ap.add_argument("--library-bars", action="store_true",
+                    help="time cuBLAS ZGEMM + ZHERK (FP64 and FP64-emulated) beside the split form, then exit")
+    ap.add_argument("--bar-reps", type=int, default=1)
     args = ap.parse_args()
 
     from workloads import make_config
@@ -243,6 +413,9 @@ def main():
     w = make_config(args.config, n_g_override=args.n_g or None)
     if args.impl == "reference":
         run_reference(args, w)
+        return
+    if args.library_bars:
+        library_bars(args, w)
         return
 
     import numpy as np
