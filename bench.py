@@ -98,6 +98,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _traffic(config: int):
+    """DRAM bytes per H/S launch of the split kernel from the committed ncu record,
+    or None when the record is for another workload or the kernel source changed."""
+    import hashlib
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        with open(os.path.join(here, "profiles", "split_gemm_dram_traffic_config4.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(here, "paper_1602_06589_gb300", "csrc", "split.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    if config != 4 or rec.get("kernel_source_sha256") != sha:
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
 def oracle_sample_time(system, kvec, m: int):
     """Oracle cost model from two bounded samples on the host cores:
     m columns with m diagonal entries (column cost), then all m^2 pairs."""
@@ -492,7 +510,9 @@ def main():
         achieved = lp_flops / (c_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "split H/S contraction (tcgen05 bf16)",
+                "traffic": _traffic(args.config) if not args.n_g else None,
+                "traffic_unit": "DRAM bytes per H/S depth-segment launch (ncu, 1 pass)",
+                "kernel": "split H/S contraction (tcgen05 bf16)",
                 "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback"}
     else:
         achieved = fal["F_HS"] / (c_ms * 1e-3) / 1e12
