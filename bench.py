@@ -194,7 +194,8 @@ def run_batched(args, w, world, rank, local, dist):
     precision = hsgen.SPLIT if args.form == "split" else hsgen.FP64
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices)
+    s_form = hsgen.S_LEGENDRE if args.s_form == "legendre" else hsgen.S_CONTRACTION
+    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form)
     kv_host = [np.ascontiguousarray(w.kvecs[k]) for k in mine]
     Hs = [torch.zeros((n, n), dtype=torch.complex128, device=dev) for n in n_gs]
     Ss = [torch.zeros_like(h) for h in Hs]
@@ -421,6 +422,8 @@ def main():
     ap.add_argument("--n-g", type=int, default=0, help="override N_G (smaller cases for profiling)")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="also time one FP64-form step on the same workload")
+    ap.add_argument("--s-form", choices=["contraction", "legendre"], default="contraction",
+                    help="S as the A^H A + B^H U B contraction (default) or in the m-summed Legendre form")
     ap.add_argument("--library-bars", action="store_true",
                     help="time cuBLAS ZGEMM + ZHERK (FP64 and FP64-emulated) beside the split form, then exit")
     ap.add_argument("--bar-reps", type=int, default=1)
@@ -469,7 +472,8 @@ def main():
     precision = hsgen.SPLIT if args.form == "split" else hsgen.FP64
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices)
+    s_form = hsgen.S_LEGENDRE if args.s_form == "legendre" else hsgen.S_CONTRACTION
+    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form)
     kv = torch.from_numpy(kv_host).to(dev)
     H = torch.zeros((n, n), dtype=torch.complex128, device=dev)
     S = torch.zeros_like(H)
@@ -504,18 +508,20 @@ def main():
 
     # dominant kernel: the H/S contraction
     c_ms = statistics.mean(contract_ms)
+    # with S in the Legendre form the contraction computes H only (half of F_HS)
+    f_contract = fal["F_HS"] / 2 if st.get("s_form") == hsgen.S_LEGENDRE else fal["F_HS"]
     if precision == hsgen.SPLIT:
         slices = st["slices"]
-        lp_flops = fal["F_HS"] * slices * (slices + 1) / 2  # bf16 products actually executed
+        lp_flops = f_contract * slices * (slices + 1) / 2  # bf16 products actually executed
         achieved = lp_flops / (c_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic(args.config) if not args.n_g else None,
+                "traffic": _traffic(args.config) if not args.n_g and st.get("s_form") != hsgen.S_LEGENDRE else None,
                 "traffic_unit": "DRAM bytes per H/S depth-segment launch (ncu, 1 pass)",
                 "kernel": "split H/S contraction (tcgen05 bf16)",
                 "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback"}
     else:
-        achieved = fal["F_HS"] / (c_ms * 1e-3) / 1e12
+        achieved = f_contract / (c_ms * 1e-3) / 1e12
         # FP64 tensor peak: measured bf16 sustained x nominal FP64/bf16 ratio (1.25 / 2250)
         peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -528,10 +534,12 @@ def main():
         "vs_baseline": None, "dtype": "bf16-split/f64" if precision == hsgen.SPLIT else "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(args.config, w), "form": args.form,
+                   "s_form": "legendre (Eq. overlap_no_m, FP64)" if st.get("s_form") == hsgen.S_LEGENDRE
+                   else "contraction",
                    "slices": st["slices"] if precision == hsgen.SPLIT else None,
                    "l2": "working set >> L2 (no flush needed)", "parallelism": f"k-point replicas x{world}"},
         "eff_tflops": eff_tflops, "flops_per_kpoint": fal["total"],
-        "phases_ms": {k: st[k] for k in ("ms_coefficients", "ms_tapply", "ms_slice", "ms_contract", "ms_total")},
+        "phases_ms": {k: st[k] for k in ("ms_coefficients", "ms_tapply", "ms_slice", "ms_contract", "ms_s", "ms_total")},
         "roofline": roof, "gpu_launches": launches,
     }
     clk_s = clk.summary()

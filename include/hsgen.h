@@ -58,6 +58,7 @@ typedef enum {
 } hsgen_status;
 
 enum { HSGEN_FP64 = 0, HSGEN_SPLIT = 1 };
+enum { HSGEN_S_CONTRACTION = 0, HSGEN_S_LEGENDRE = 1 };
 
 typedef struct {
   int precision;            /* HSGEN_FP64 (default) or HSGEN_SPLIT                  */
@@ -68,6 +69,11 @@ typedef struct {
   int fill_full;            /* 1: also write the other triangle (Hermitian mirror)  */
   int atom_chunk;           /* atoms per pass over the depth, 0 = all at once       */
   long long wait_timeout_ns; /* limit of every device-side wait (default 2e9)       */
+  int s_form;               /* HSGEN_S_CONTRACTION (default): S = sum_a A^H A +    */
+                            /* B^H U B in the chosen precision; HSGEN_S_LEGENDRE:  */
+                            /* the m-summed form of Sec. 3.1 (Eq. overlap_no_m) in */
+                            /* FP64, used when all K_t lie on one lattice k + G,   */
+                            /* otherwise the contraction (see hsgen_stats.s_form)  */
 } hsgen_options;
 
 /* Radial data of one atom species (App. A.1 and A.2). All arrays are host
@@ -102,6 +108,8 @@ typedef struct {
   int n_kpoints;           /* k-points in the last call                         */
   long long workspace_bytes; /* device workspace currently held                 */
   long long kernel_launches; /* kernels the last call launched                   */
+  int s_form;              /* how the last call built S (HSGEN_S_*)             */
+  double ms_s;             /* S in the Legendre form (0 otherwise)              */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */

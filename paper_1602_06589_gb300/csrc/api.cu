@@ -108,6 +108,7 @@ hsgen_status hsgen_default_options(hsgen_options *opt) {
   opt->fill_full = 0;
   opt->atom_chunk = 0;
   opt->wait_timeout_ns = 2000000000LL;
+  opt->s_form = HSGEN_S_CONTRACTION;
   return HSGEN_OK;
 }
 
@@ -121,6 +122,7 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   if (o.uplo != 'U' && o.uplo != 'L') return HSGEN_EINVAL;
   if (o.atom_chunk < 0 || o.slices < 0 || o.slices > kMaxSlices) return HSGEN_EINVAL;
   if (!(o.target_rel_err > 0.0) || o.wait_timeout_ns <= 0) return HSGEN_EINVAL;
+  if (o.s_form != HSGEN_S_CONTRACTION && o.s_form != HSGEN_S_LEGENDRE) return HSGEN_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -336,6 +338,7 @@ struct KpointJob {
   const double *kvec_dev;
   double2 *H, *S;
   long long ld;
+  const LegendrePlan *leg = nullptr;  // S in the Legendre form (else the contraction)
 };
 
 // Device workspace layout for one k-point (byte offsets).
@@ -402,8 +405,8 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
     }
     if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
     if (split) {
-      hsgen_status st = split_chunk(ctx, n_g, a0, a1, W, X, L.ldw, job.H, job.S, job.ld, ci > 0, ws + L.split,
-                                    slices, s, rec);
+      hsgen_status st = split_chunk(ctx, n_g, a0, a1, W, X, L.ldw, job.H, job.leg ? nullptr : job.S, job.ld,
+                                    ci > 0, ws + L.split, slices, s, rec);
       if (st != HSGEN_OK) return st;
     } else {
       for (int t = 0; t < nt; ++t) {
@@ -419,11 +422,16 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
       }
       if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
       if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
-      HSG_LAUNCH(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H, job.S, job.ld,
-                                     ctx->opt.uplo, ci > 0 ? 1 : 0, s));
+      HSG_LAUNCH(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H,
+                                     job.leg ? nullptr : job.S, job.ld, ctx->opt.uplo, ci > 0 ? 1 : 0, s));
     }
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
+  if (job.leg) {
+    hsgen_status st = legendre_S(ctx, n_g, job.kvec_dev, F, *job.leg, ctx->ws_leg.ptr, job.S, job.ld, s);
+    if (st != HSGEN_OK) return st;
+    if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
+  }
   if (ctx->opt.fill_full) {
     HSG_LAUNCH(ctx, launch_mirror(n_g, job.H, job.ld, ctx->opt.uplo, s));
     HSG_LAUNCH(ctx, launch_mirror(n_g, job.S, job.ld, ctx->opt.uplo, s));
@@ -538,6 +546,22 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
     // host outputs are written in full: the other triangle is zero unless fill_full
     HSG_CUDA(ctx, cudaMemsetAsync(ctx->ws_out.ptr, 0, 2 * hs_bytes, s));
   }
+  LegendrePlan plan;
+  if (ctx->opt.s_form == HSGEN_S_LEGENDRE) {
+    std::vector<double> kh;
+    const double *kp = kvec;
+    if (kdev) {
+      kh.resize(3 * (size_t)n_g);
+      HSG_CUDA(ctx, cudaMemcpyAsync(kh.data(), kvec, sizeof(double) * kh.size(), cudaMemcpyDeviceToHost, s));
+      HSG_CUDA(ctx, cudaStreamSynchronize(s));
+      kp = kh.data();
+    }
+    if (legendre_plan(ctx, n_g, kp, plan)) {
+      st = ensure_ws(ctx, ctx->ws_leg, legendre_ws_bytes(ctx, n_g, plan));
+      if (st != HSGEN_OK) return st;
+      job.leg = &plan;
+    }
+  }
   ctx->launches = 0;
   st = run_kpoint(ctx, job, s, ws, L, true);
   if (st != HSGEN_OK) return st;
@@ -554,8 +578,10 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   ctx->stats.n_kpoints = 1;
   ctx->stats.flops_algorithmic = algorithmic_flops(ctx, n_g);
   ctx->stats.kernel_launches = ctx->launches;
+  ctx->stats.s_form = job.leg ? HSGEN_S_LEGENDRE : HSGEN_S_CONTRACTION;
   ctx->phase_used[0] = atom_chunks(ctx).size() == 1;
   ctx->phase_used[1] = 1;
+  ctx->phase_used[2] = job.leg != nullptr;
   return HSGEN_OK;
 }
 
@@ -596,7 +622,7 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   if (!ctx || !out) return HSGEN_EINVAL;
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
   hsgen_stats st = ctx->stats;
-  st.ms_coefficients = st.ms_tapply = st.ms_slice = st.ms_contract = st.ms_total = 0.0;
+  st.ms_coefficients = st.ms_tapply = st.ms_slice = st.ms_contract = st.ms_total = st.ms_s = 0.0;
   if (ctx->phase_used[1]) {
     float ms = 0.f;
     HSG_CUDA(ctx, cudaEventSynchronize(ctx->ev[5]));
@@ -607,9 +633,10 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
       if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) == cudaSuccess) st.ms_slice = ms;
       if (cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]) == cudaSuccess) st.ms_contract = ms;
     }
+    if (ctx->phase_used[2] && cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[6]) == cudaSuccess) st.ms_s = ms;
     cudaGetLastError();
   }
-  st.workspace_bytes = (long long)(ctx->ws_main.bytes + ctx->ws_out.bytes);
+  st.workspace_bytes = (long long)(ctx->ws_main.bytes + ctx->ws_out.bytes + ctx->ws_leg.bytes);
   *out = st;
   return HSGEN_OK;
 }
@@ -626,6 +653,7 @@ void hsgen_destroy(hsgen_ctx *ctx) {
   split_release(ctx);
   if (ctx->ws_main.ptr) cudaFree(ctx->ws_main.ptr);
   if (ctx->ws_out.ptr) cudaFree(ctx->ws_out.ptr);
+  if (ctx->ws_leg.ptr) cudaFree(ctx->ws_leg.ptr);
   if (ctx->events_ready)
     for (auto &e : ctx->ev) cudaEventDestroy(e);
   delete ctx;

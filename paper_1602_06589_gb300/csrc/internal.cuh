@@ -73,6 +73,7 @@ struct hsgen_ctx {
   // workspaces
   hsg::Workspace ws_main;           // W, X, radial factors, kvec copy, split slices
   hsg::Workspace ws_out;            // device H/S staging when the caller passes host pointers
+  hsg::Workspace ws_leg;            // S in the Legendre form: coordinates, structure factors, tables
   int split_slices = 0;             // slices the species' T were cut into
   int *d_status = nullptr;          // device status word of the split kernels
   int *h_status = nullptr;          // pinned host copy
@@ -117,6 +118,24 @@ cudaError_t launch_radial(int n_g, const double *kvec, int n_types, const Radial
 cudaError_t launch_coefficients(int lmax, int n_g, const double *kvec, const double2 *F_type, const int *atoms,
                                 int n_atoms, const double *pos, const double *rot, const int *off,
                                 int row_base, int dpad, double2 *W, long long ldw, cudaStream_t s);
+// S in the m-summed (Legendre) form (Sec. 3.1, Eq. overlap_no_m): the plan
+// holds each plane wave's integer reciprocal-lattice coordinates relative to
+// K_0 (shifted to start at 0) and the box of their differences; `ok` is false
+// when the K_t do not lie on one lattice k + G or the tables would be too large.
+struct LegendrePlan {
+  bool ok = false;
+  std::vector<int> nco;  // 3 per plane wave
+  int span[3] = {0, 0, 0}, dim[3] = {1, 1, 1};
+  long long cells = 1;
+  int lmax = 0;
+};
+bool legendre_plan(const hsgen_ctx *ctx, int n_g, const double *kvec_host, LegendrePlan &p);
+size_t legendre_ws_bytes(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p);
+// Writes the opt.uplo triangle of S (device, ld) from the radial factors F of
+// this k-point (F[type][t][l], as launch_radial writes them); ws holds
+// legendre_ws_bytes. Asynchronous on s (host tables are staged by the copies).
+hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const double2 *F, const LegendrePlan &p,
+                        void *ws, double2 *S, long long ld, cudaStream_t s);
 // a2: T matrix of one species (device, dpad x dpad complex, column-major).
 cudaError_t launch_tmatrix(const Species &sp, double2 *d_T, double *scratch, cudaStream_t s);
 // Recurrence tables in constant memory (called once per device).

@@ -919,12 +919,13 @@ hsgen_status tapply_split(hsgen_ctx *ctx, int n_g, int a0, int a1, const __nv_bf
 }
 
 // One H problem (H = W^H X) and one S problem (S = (U W)^H W) of one k-point
-// over the depth segment [kb0, kb0 + seg) of 64-deep blocks.
+// over the depth segment [kb0, kb0 + seg) of 64-deep blocks; S == nullptr:
+// the H problem only (S is built in the Legendre form).
 bool hs_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, long long ldk, int kb0, int seg,
                  bool accumulate, int uplo, const __nv_bfloat16 *Wsl, const __nv_bfloat16 *Xsl,
                  const __nv_bfloat16 *Ysl, const int *expW, const int *expX, const int *expY, double2 *H, double2 *S,
                  long long ld, const int2 *tiles, long long ntiles, long long tile_begin, int slices) {
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < (S ? 2 : 1); ++k) {
     GemmProblem &q = pr[k];
     std::memset(&q, 0, sizeof(q));
     q.M = n_g;
@@ -1038,8 +1039,9 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
   // (3) X slices (right operand of H) and (U W) slices (left operand of S)
   HSG_LAUNCH(ctx, launch_slice(X, ldw, cdepth, nullptr, slices, 3, w.Xsl, w.ldk, plane, w.expX, n_g, s));
-  HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, ctx->d_urow + row_base, slices, 2, w.Ysl, w.ldk, plane, w.expY,
-                               n_g, s));
+  if (S)
+    HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, ctx->d_urow + row_base, slices, 2, w.Ysl, w.ldk, plane, w.expY,
+                                 n_g, s));
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
   // (4) H = W^H X and S = (U W)^H W over one triangle
   {
@@ -1071,8 +1073,8 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
     if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, w.ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
                      w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles, per, 0, slices))
       return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
-    P.nprob = 2;
-    P.ntiles = 2 * per;
+    P.nprob = S ? 2 : 1;
+    P.ntiles = P.nprob * per;
     HSG_LAUNCH(ctx, launch_gemm(P, s));
     }
   }
@@ -1101,6 +1103,7 @@ hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s) {
 hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec, void *const *H,
                            void *const *S, const long long *ld, cudaStream_t s) {
   if (ctx->opt.precision != HSGEN_SPLIT) return HSGEN_ENOTSUP;
+  if (ctx->opt.s_form == HSGEN_S_LEGENDRE) return HSGEN_ENOTSUP;  // k-point by k-point
   const int na = (int)ctx->toa.size();
   if (ctx->opt.atom_chunk > 0 && ctx->opt.atom_chunk < na) return HSGEN_ENOTSUP;
   if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: no system set");
@@ -1342,6 +1345,8 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   ctx->stats.precision = HSGEN_SPLIT;
   ctx->phase_used[0] = 0;
   ctx->phase_used[1] = 0;
+  ctx->phase_used[2] = 0;
+  ctx->stats.s_form = HSGEN_S_CONTRACTION;
   return split_check_status(ctx, s);
 }
 

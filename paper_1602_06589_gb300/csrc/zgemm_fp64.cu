@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(NTHREADS) tapply_kernel(int dpad, int n_g, con
   store_tile(X + r0, ldw, dpad, n_g, blockIdx.x * MT, blockIdx.y * NT, acc, 0, 0);
 }
 
-// a4: one CTA per tile of the chosen triangle (linear index -> (bi, bj)).
+// a4: one CTA per tile of the chosen triangle (linear index -> (bi, bj));
+// WITH_S false: H only (S is built in the Legendre form).
+template <bool WITH_S>
 __global__ void __launch_bounds__(NTHREADS) hs_kernel(int n_g, int depth, const double2 *__restrict__ W,
                                                       const double2 *__restrict__ X, const double *__restrict__ urow,
                                                       long long ldw, double2 *__restrict__ H, double2 *__restrict__ S,
@@ -191,10 +193,10 @@ __global__ void __launch_bounds__(NTHREADS) hs_kernel(int n_g, int depth, const 
   int bi = (uplo == 'U') ? lo : hi, bj = (uplo == 'U') ? hi : lo;
   double acc1[4][2][2][2], acc2[4][2][2][2];
   zero_acc<true>(acc1);
-  zero_acc<true>(acc2);
-  tile_mma<true>(W, ldw, X, ldw, urow, n_g, n_g, depth, bi * MT, bj * NT, acc1, acc2, smem);
+  zero_acc<WITH_S>(acc2);
+  tile_mma<WITH_S>(W, ldw, X, ldw, urow, n_g, n_g, depth, bi * MT, bj * NT, acc1, acc2, smem);
   store_tile(H, ld, n_g, n_g, bi * MT, bj * NT, acc1, uplo, accumulate);
-  store_tile(S, ld, n_g, n_g, bi * MT, bj * NT, acc2, uplo, accumulate);
+  if (WITH_S) store_tile(S, ld, n_g, n_g, bi * MT, bj * NT, acc2, uplo, accumulate);
 }
 
 __global__ void mirror_kernel(int n, double2 *M, long long ld, int uplo) {
@@ -231,14 +233,19 @@ cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *
   size_t sm = sizeof(double2) * 2 * 3 * KT * PADS;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(hs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(hs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(hs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   long long nb = (n_g + MT - 1) / MT;
   long long ntiles = nb * (nb + 1) / 2;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  hs_kernel<<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate);
+  if (S)
+    hs_kernel<true><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate);
+  else
+    hs_kernel<false><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate);
   return cudaGetLastError();
 }
 

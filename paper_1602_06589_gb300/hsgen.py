@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libhsgen.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENUMERIC = range(7)
 FP64, SPLIT = 0, 1
+S_CONTRACTION, S_LEGENDRE = 0, 1
 STATUS_NAMES = {0: "HSGEN_OK", 1: "HSGEN_EINVAL", 2: "HSGEN_ENOMEM", 3: "HSGEN_ECUDA", 4: "HSGEN_ETIMEOUT",
                 5: "HSGEN_ENOTSUP", 6: "HSGEN_ENUMERIC"}
 
@@ -31,7 +32,8 @@ _ip = C.POINTER(C.c_int)
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("target_rel_err", C.c_double), ("slices", C.c_int), ("uplo", C.c_int),
-                ("fill_full", C.c_int), ("atom_chunk", C.c_int), ("wait_timeout_ns", C.c_longlong)]
+                ("fill_full", C.c_int), ("atom_chunk", C.c_int), ("wait_timeout_ns", C.c_longlong),
+                ("s_form", C.c_int)]
 
 
 class TypeDesc(C.Structure):
@@ -44,7 +46,8 @@ class Stats(C.Structure):
     _fields_ = [("ms_coefficients", C.c_double), ("ms_tapply", C.c_double), ("ms_slice", C.c_double),
                 ("ms_contract", C.c_double), ("ms_total", C.c_double), ("flops_algorithmic", C.c_double),
                 ("precision", C.c_int), ("slices", C.c_int), ("n_kpoints", C.c_int),
-                ("workspace_bytes", C.c_longlong), ("kernel_launches", C.c_longlong)]
+                ("workspace_bytes", C.c_longlong), ("kernel_launches", C.c_longlong), ("s_form", C.c_int),
+                ("ms_s", C.c_double)]
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
@@ -220,7 +223,7 @@ class Generator:
 
     def __init__(self, system, device: int = 0, precision: int = FP64, slices: int = 0,
                  target_rel_err: float = 1e-12, uplo: str = "U", fill_full: bool = False, atom_chunk: int = 0,
-                 wait_timeout_ns: int = 2_000_000_000):
+                 wait_timeout_ns: int = 2_000_000_000, s_form: int = S_CONTRACTION):
         o = hsgen_default_options()
         o.precision = precision
         o.slices = slices
@@ -229,6 +232,7 @@ class Generator:
         o.fill_full = int(fill_full)
         o.atom_chunk = atom_chunk
         o.wait_timeout_ns = wait_timeout_ns
+        o.s_form = s_form
         self.device = device
         self.system = system
         self.ctx = hsgen_create(device, o)

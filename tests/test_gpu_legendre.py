@@ -1,0 +1,197 @@
+"""GPU parity of S in the m-summed (Legendre) form (Sec. 3.1, Eq.
+overlap_no_m) against the oracle's S (the matrix form of Eq. def_overlap),
+through the C ABI, in both precisions of the H contraction.
+
+S in this form is FP64 arithmetic throughout: relative Frobenius error
+<= 1e-12 over the written triangle and <= 1e-10 per entry relative to
+||w_i|| ||y_j|| (y = U w). H is computed by the unchanged contraction and must equal
+the contraction-only build bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import make_config, make_system, kpoint_list
+
+from _parity import compare, normwise_scales, tri_mask
+
+pytestmark = pytest.mark.gpu
+
+REL_F = 1e-12
+PER_ENTRY = 1e-10
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1602_06589_gb300 import hsgen
+
+    assert torch.cuda.is_available()
+    return hsgen
+
+
+def mixed_system(seed=3, lmaxes=(2, 4, 0), counts=(2, 1, 2), cell=10.0):
+    lat = np.array([[cell, 0.3, 0.0], [0.0, cell * 1.1, 0.2], [0.1, 0.0, cell * 0.95]])
+    species = [(lm, 1.5 + 0.1 * i) for i, lm in enumerate(lmaxes)]
+    return make_system(seed, lat, species, list(counts))
+
+
+def build(hs, system, kv, **kw):
+    import torch
+
+    with hs.Generator(system, **kw) as g:
+        H, S = g.build(torch.from_numpy(kv).cuda())
+        torch.cuda.synchronize()
+        return H.cpu().numpy(), S.cpu().numpy(), g.stats()
+
+
+def check_S(system, kv, S, uplo="U", full=False):
+    _, So = oracle.build_HS(system, kv, full=True)
+    wn, _, yn = normwise_scales(system, kv)
+    n = kv.shape[0]
+    mask = np.ones((n, n), bool) if full else tri_mask(n, uplo)
+    rf, pe = compare(S, So, wn, yn, mask)
+    assert rf <= REL_F and pe <= PER_ENTRY, (rf, pe)
+    if not full:
+        assert np.all(S[~mask] == 0)
+    assert np.all(np.diag(S).imag == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["SPLIT", "FP64"])
+def test_legendre_config0(hs, precision):
+    w = make_config(0)
+    kv = w.kvecs[0]
+    p = getattr(hs, precision)
+    H1, S1, st = build(hs, w.system, kv, precision=p, s_form=hs.S_LEGENDRE)
+    assert st["s_form"] == hs.S_LEGENDRE and st["ms_s"] > 0.0
+    check_S(w.system, kv, S1)
+    H0, _, st0 = build(hs, w.system, kv, precision=p)
+    assert st0["s_form"] == hs.S_CONTRACTION
+    assert np.array_equal(H1, H0)
+
+
+@pytest.mark.parametrize("n_g", [1, 7, 129, 300])
+def test_legendre_ragged_mixed_lmax(hs, n_g):
+    sysm = mixed_system()
+    kv = kpoint_list(sysm.lattice, (0.13, -0.07, 0.21), n_g)
+    _, S, st = build(hs, sysm, kv, precision=hs.SPLIT, s_form=hs.S_LEGENDRE)
+    assert st["s_form"] == hs.S_LEGENDRE
+    check_S(sysm, kv, S)
+
+
+def test_legendre_gamma_lower_full_chunked(hs):
+    """K = 0 is in the set at Gamma (its direction is undefined: only l = 0 survives)."""
+    sysm = mixed_system(seed=9, counts=(3, 2, 2))
+    kv = kpoint_list(sysm.lattice, (0.0, 0.0, 0.0), 160)
+    assert np.any(np.all(kv == 0.0, axis=1))
+    _, S, _ = build(hs, sysm, kv, precision=hs.SPLIT, s_form=hs.S_LEGENDRE)
+    check_S(sysm, kv, S)
+    _, S, _ = build(hs, sysm, kv, precision=hs.FP64, s_form=hs.S_LEGENDRE, uplo="L")
+    check_S(sysm, kv, S, uplo="L")
+    _, S, _ = build(hs, sysm, kv, precision=hs.SPLIT, s_form=hs.S_LEGENDRE, fill_full=True)
+    check_S(sysm, kv, S, full=True)
+    _, S, _ = build(hs, sysm, kv, precision=hs.SPLIT, s_form=hs.S_LEGENDRE, atom_chunk=3)
+    check_S(sysm, kv, S)
+
+
+def test_legendre_host_pointers(hs):
+    sysm = mixed_system(seed=13)
+    kv = np.ascontiguousarray(kpoint_list(sysm.lattice, (0.1, 0.2, 0.3), 90))
+    n = kv.shape[0]
+    H = np.zeros((n, n), np.complex128)
+    S = np.zeros((n, n), np.complex128)
+    with hs.Generator(sysm, precision=hs.SPLIT, s_form=hs.S_LEGENDRE) as g:
+        hs.hsgen_build_HS(g.ctx, n, kv.ctypes.data, H.ctypes.data, S.ctypes.data, n, 0)
+        assert g.stats()["s_form"] == hs.S_LEGENDRE
+    check_S(sysm, kv, S.T)
+
+
+def test_legendre_off_lattice_falls_back(hs):
+    """Plane waves that are not k + G of one lattice: S comes from the contraction."""
+    sysm = mixed_system(seed=17)
+    kv = kpoint_list(sysm.lattice, (0.1, 0.0, 0.2), 120).copy()
+    kv[5] += np.array([1e-3, 0.0, 0.0])
+    _, S, st = build(hs, sysm, kv, precision=hs.FP64, s_form=hs.S_LEGENDRE)
+    assert st["s_form"] == hs.S_CONTRACTION and st["ms_s"] == 0.0
+    check_S(sysm, kv, S)
+
+
+def test_legendre_complex_T_override_leaves_S(hs):
+    """S does not involve T: a complex T changes H only."""
+    sysm = mixed_system(seed=21)
+    rng = np.random.default_rng(3)
+    for ty in sysm.types:
+        n = 2 * ty.nl
+        A = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+        ty.T_override = 0.5 * (A + A.conj().T)
+    kv = kpoint_list(sysm.lattice, (0.1, 0.0, 0.2), 140)
+    _, S, _ = build(hs, sysm, kv, precision=hs.SPLIT, s_form=hs.S_LEGENDRE)
+    check_S(sysm, kv, S)
+
+
+def test_legendre_config1(hs):
+    w = make_config(1)
+    _, S, st = build(hs, w.system, w.kvecs[0], precision=hs.SPLIT, s_form=hs.S_LEGENDRE)
+    assert st["s_form"] == hs.S_LEGENDRE
+    check_S(w.system, w.kvecs[0], S)
+
+
+def test_legendre_batched_matches_single(hs):
+    import torch
+
+    w = make_config(3)
+    ks = [w.kvecs[i] for i in (0, 7, 21)]
+    with hs.Generator(w.system, precision=hs.SPLIT, s_form=hs.S_LEGENDRE) as g:
+        singles = [tuple(x.clone() for x in g.build(torch.from_numpy(k).cuda())) for k in ks]
+        Hs = [torch.zeros((k.shape[0],) * 2, dtype=torch.complex128, device="cuda") for k in ks]
+        Ss = [torch.zeros_like(h) for h in Hs]
+        kvs = [np.ascontiguousarray(k) for k in ks]
+        hs.hsgen_build_HS_batched(g.ctx, [k.shape[0] for k in ks], [k.ctypes.data for k in kvs],
+                                  [h.data_ptr() for h in Hs], [s.data_ptr() for s in Ss], [k.shape[0] for k in ks])
+        torch.cuda.synchronize()
+        for (H1, S1), H2, S2 in zip(singles, Hs, Ss):
+            assert torch.equal(H1, H2.mT) and torch.equal(S1, S2.mT)
+
+
+def sampled_S(hs, cfg, n_samp=14, seed=0):
+    import torch
+
+    import _parity
+
+    w = make_config(cfg)
+    kv = w.kvecs[0]
+    n = kv.shape[0]
+    with hs.Generator(w.system, precision=hs.SPLIT, s_form=hs.S_LEGENDRE) as g:
+        _, S = g.build(torch.from_numpy(kv).cuda())
+        torch.cuda.synchronize()
+        assert g.stats()["s_form"] == hs.S_LEGENDRE
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(n, n_samp, replace=False))
+        idx[0], idx[-1] = 0, n - 1
+        idx = np.unique(idx)
+        r, c = np.meshgrid(idx, idx, indexing="ij")
+        sel = r <= c
+        Sg = S[torch.from_numpy(r[sel]).cuda(), torch.from_numpy(c[sel]).cuda()].cpu().numpy()
+    _, So = oracle.HS_entries(w.system, kv, r[sel], c[sel])
+    Wc, _, Yc = _parity.oracle_columns(w.system, kv[idx])
+    pos = {v: i for i, v in enumerate(idx)}
+    ri = np.array([pos[v] for v in r[sel]])
+    ci = np.array([pos[v] for v in c[sel]])
+    wn, yn = np.linalg.norm(Wc, axis=0), np.linalg.norm(Yc, axis=0)
+    rel = np.linalg.norm(Sg - So) / np.linalg.norm(So)
+    per = np.max(np.abs(Sg - So) / (wn[ri] * yn[ci]))
+    assert rel <= REL_F and per <= PER_ENTRY, (rel, per)
+
+
+def test_legendre_config2_sampled(hs):
+    sampled_S(hs, 2)
+
+
+@pytest.mark.slow
+def test_legendre_config4_sampled(hs):
+    """256 atoms, l_max 10, N_G 20000."""
+    sampled_S(hs, 4, n_samp=12)
