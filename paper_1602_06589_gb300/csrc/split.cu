@@ -36,10 +36,11 @@
 // read both CTAs' shared memory and write each CTA's 128 rows into its own
 // tensor memory.
 //
-// Kernel roles (320 threads per CTA, one CTA per SM, persistent over tiles):
-//   warp 0     TMA producer (cp.async.bulk.tensor, 128B swizzle, 3 stages of 2 k-blocks)
-//   warp 1     TMEM allocator; tcgen05.mma issuer in the leader CTA
-//   warps 2-9  epilogue (TMEM lane quadrant = warp % 4, real or imaginary half)
+// Kernel roles (384 threads per CTA, one CTA per SM, persistent over tiles):
+//   warps 0-7   epilogue (TMEM lane quadrant = warp % 4, real or imaginary half)
+//   warp 8      TMA producer (cp.async.bulk.tensor, 128B swizzle, 3 stages of 2 k-blocks)
+//   warp 9      TMEM allocator; tcgen05.mma issuer in the leader CTA
+//   warps 10-11 idle (their registers go to the epilogue)
 // Every wait is bounded (wait_timeout_ns); on expiry the kernel records an
 // error word, drains its own copies and MMAs (again bounded), frees TMEM and
 // returns, and the host reports HSGEN_ETIMEOUT.
@@ -70,7 +71,16 @@ constexpr int A_BYTES = 16384;                 // one k-block of A: 128x64 bf16 
 constexpr int B_BYTES = 16384;                 // one k-block of this CTA's half of B: 128x64 bf16
 constexpr int STAGE_A = KPS * A_BYTES;         // A k-blocks of a stage, then its B k-blocks
 constexpr int STAGE_BYTES = KPS * (A_BYTES + B_BYTES);
-constexpr int NTHREADS = 320;           // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+// warps 0-7 epilogue (warpgroups 0, 1), warp 8 TMA, warp 9 MMA, warps 10-11 idle
+// (warpgroup 2, which hands its registers to the epilogue)
+constexpr int NTHREADS = 384;
+constexpr int WARP_TMA = 8, WARP_MMA = 9;
+// Register split (setmaxnreg): the CTA is launched with 168 registers per
+// thread (65536 / 384 rounded down to 8), 384 x 168 = 64512 in all;
+// warpgroup 2 drops to 72 and the two epilogue warpgroups rise to 216:
+// 256 x 216 + 128 x 72 = 64512, so the epilogue's int64 sums need no spills.
+constexpr int REG_LAUNCH = 168, REG_EPI = 216, REG_AUX = 72;
+static_assert(2 * 128 * REG_EPI + 128 * REG_AUX <= NTHREADS * REG_LAUNCH, "register split exceeds the launch");
 constexpr int NACC = 2;                 // FP32 accumulator buffers of 256 TMEM columns
 constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024 + 256;  // 197888 <= 232448 (227 KiB)
 constexpr uint32_t TMEM_COLS = 512;
@@ -380,7 +390,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == WARP_MMA) {
     tc_alloc(smem_u32(tmem_slot), TMEM_COLS);
     tc_relinquish();
   }
@@ -392,8 +402,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
   const int S = P.s;
   // teardown waits: long enough for copies and MMAs already issued to finish
   const unsigned long long drain = tmo > 1000000000ull ? tmo : 1000000000ull;
-
-  if (warp == 0) {
+  if (warp == WARP_TMA) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_AUX));
     // ------------------------------ TMA producer ------------------------------
     uint32_t it = 0;
     bool ok = true;
@@ -463,7 +473,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const uint32_t j = st + NST * ((it - 1 - st) / NST);
       if (!warp_wait(full0 + 8 * st, (j / NST) & 1, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
     }
-  } else if (warp == 1 && leader) {
+  } else if (warp == WARP_MMA) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_AUX));
+    if (leader) {
     // ------------------------------ MMA issuer --------------------------------
     const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + STAGE_A);
     uint32_t it = 0, cc = 0;
@@ -531,15 +543,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     if (elect_one()) tc_commit(tdown);
     __syncwarp();
     if (!warp_wait(tdown, 0, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
-  } else if (warp >= 2) {
+    }
+  } else if (warp < WARP_TMA) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_EPI));
     // ------------------------------ epilogue ----------------------------------
     // Eight warps: warp w reads TMEM lane quadrant w % 4 (rows), and half hf of
     // the accumulator columns (hf 0: real parts, hf 1: imaginary parts of the
     // tile's 64 complex columns). The int64 fixed-point sums live in registers
     // for the whole tile.
-    const int ew = warp - 2;
     const int qd = warp & 3;
-    const int hf = ew >> 2;
+    const int hf = warp >> 2;
     const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
     uint32_t cc = 0;
     bool ok = true;
@@ -622,12 +635,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         }
       }
     }
+  } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_AUX));
   }
   tc_fence_before();
   __syncthreads();
   cluster_sync();  // the leader's MMAs and both CTAs' copies are complete
   tc_fence_after();
-  if (warp == 1) tc_dealloc(tbase, TMEM_COLS);
+  if (warp == WARP_MMA) tc_dealloc(tbase, TMEM_COLS);
 }
 
 // ---------------------------------------------------------------------------
