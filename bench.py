@@ -422,6 +422,8 @@ def main():
     ap.add_argument("--n-g", type=int, default=0, help="override N_G (smaller cases for profiling)")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="also time one FP64-form step on the same workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip hsgen_autotune before the warm-up (split form)")
     ap.add_argument("--s-form", choices=["contraction", "legendre"], default="contraction",
                     help="S as the A^H A + B^H U B contraction (default) or in the m-summed Legendre form")
     ap.add_argument("--library-bars", action="store_true",
@@ -477,6 +479,9 @@ def main():
     kv = torch.from_numpy(kv_host).to(dev)
     H = torch.zeros((n, n), dtype=torch.complex128, device=dev)
     S = torch.zeros_like(H)
+    if precision == hsgen.SPLIT and not args.no_autotune:
+        g.autotune(kv, H, S)  # untimed: picks the depth segment and tile band for this shape
+    tuned = g.stats()
     for _ in range(args.warmup):
         g.build(kv, H, S)
     torch.cuda.synchronize()
@@ -537,6 +542,8 @@ def main():
                    "s_form": "legendre (Eq. overlap_no_m, FP64)" if st.get("s_form") == hsgen.S_LEGENDRE
                    else "contraction",
                    "slices": st["slices"] if precision == hsgen.SPLIT else None,
+                   "schedule": ({"kseg_blocks": tuned["kseg_blocks"], "tile_band": tuned["tile_band"],
+                                 "autotuned": not args.no_autotune} if precision == hsgen.SPLIT else None),
                    "l2": "working set >> L2 (no flush needed)", "parallelism": f"k-point replicas x{world}"},
         "eff_tflops": eff_tflops, "flops_per_kpoint": fal["total"],
         "phases_ms": {k: st[k] for k in ("ms_coefficients", "ms_tapply", "ms_slice", "ms_contract", "ms_s", "ms_total")},

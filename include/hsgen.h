@@ -110,6 +110,8 @@ typedef struct {
   long long kernel_launches; /* kernels the last call launched                   */
   int s_form;              /* how the last call built S (HSGEN_S_*)             */
   double ms_s;             /* S in the Legendre form (0 otherwise)              */
+  int kseg_blocks;         /* split form: depth segment (64-deep blocks) in use */
+  int tile_band;           /* split form: column blocks per tile band in use    */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -178,6 +180,16 @@ hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T);
  * block of atom a is offsets[a] .. offsets[a] + 2 N_La (A rows, then B rows),
  * followed by zero rows up to offsets[a+1]. */
 hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
+
+/* Autotuner of the split form's schedule (no counterpart in the paper):
+ * times hsgen_build_HS on this k-point for depth-segment lengths
+ * {64, 96, 128, 192} blocks of 64 (tile band 16), then tile bands {8, 32}
+ * with the best segment, keeps the fastest pair in the context for later
+ * builds (batched ones included) and leaves H and S built with it. Same
+ * arguments as hsgen_build_HS; synchronous; about eight builds long. The
+ * FP64 form has nothing to tune: it builds once and returns HSGEN_OK. */
+hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
+                            void *cuda_stream);
 
 hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *stats);
 const char *hsgen_last_error(const hsgen_ctx *ctx);

@@ -618,6 +618,57 @@ hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, con
   return HSGEN_OK;
 }
 
+hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
+                            void *cuda_stream) {
+  if (!ctx) return HSGEN_EINVAL;
+  if (ctx->opt.precision != HSGEN_SPLIT) return hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // one timed build per candidate (device time of the whole build); the
+  // first is preceded by an untimed build that sets up the workspaces
+  bool warm = false;
+  auto trial = [&](int kseg, int band, double &ms) -> hsgen_status {
+    ctx->kseg_blocks = kseg;
+    ctx->tile_band = band;
+    hsgen_status st = HSGEN_OK;
+    if (!warm) {
+      st = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+      if (st != HSGEN_OK) return st;
+      warm = true;
+    }
+    st = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+    if (st != HSGEN_OK) return st;
+    HSG_CUDA(ctx, cudaStreamSynchronize(s));
+    float t = 0.f;
+    HSG_CUDA(ctx, cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[5]));
+    ms = t;
+    return HSGEN_OK;
+  };
+  int best_k = ctx->kseg_blocks, best_b = ctx->tile_band;
+  double best = 1e300;
+  for (int kseg : {128, 64, 96, 192}) {
+    double ms = 0.0;
+    hsgen_status st = trial(kseg, 16, ms);
+    if (st != HSGEN_OK) return st;
+    if (ms < best) {
+      best = ms;
+      best_k = kseg;
+      best_b = 16;
+    }
+  }
+  for (int band : {8, 32}) {
+    double ms = 0.0;
+    hsgen_status st = trial(best_k, band, ms);
+    if (st != HSGEN_OK) return st;
+    if (ms < best) {
+      best = ms;
+      best_b = band;
+    }
+  }
+  ctx->kseg_blocks = best_k;
+  ctx->tile_band = best_b;
+  return hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+}
+
 hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   if (!ctx || !out) return HSGEN_EINVAL;
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -637,6 +688,8 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
     cudaGetLastError();
   }
   st.workspace_bytes = (long long)(ctx->ws_main.bytes + ctx->ws_out.bytes + ctx->ws_leg.bytes);
+  st.kseg_blocks = ctx->kseg_blocks;
+  st.tile_band = ctx->tile_band;
   *out = st;
   return HSGEN_OK;
 }

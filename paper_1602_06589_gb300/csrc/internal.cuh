@@ -81,6 +81,8 @@ struct hsgen_ctx {
   int tiles_n = -1, tiles_uplo = 0;
   long long tiles_count = 0;
   int kseg_blocks = 128;            // split form: k-blocks (64 deep) per H/S launch
+  int tile_band = 16;               // split form: column blocks per band of the tile order
+  int tiles_band = 0;               // band the cached tile list was built with
   hsg::Workspace ws_batch;          // batched k-points: per-k slices, tables, shared scratch
   cudaGraphExec_t batch_exec = nullptr;  // captured kernel sequence of the last batch
   cudaStream_t capture_stream = nullptr; // private stream the batch sequence is captured on

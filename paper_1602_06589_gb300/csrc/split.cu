@@ -889,11 +889,11 @@ SplitWs split_ws_layout(void *base, int n_g, int depth, int s) {
   return w;
 }
 
-// Tiles of one triangle, in bands of kBand column blocks: within a band all
+// Tiles of one triangle, in bands of `band` column blocks: within a band all
 // row blocks in order, so the ~one wave of tiles that runs at a time shares a
-// few A row blocks and kBand B column blocks through L2.
-std::vector<int2> tri_tiles(int n, int uplo) {
-  constexpr int kBand = 16;
+// few A row blocks and `band` B column blocks through L2.
+std::vector<int2> tri_tiles(int n, int uplo, int band) {
+  const int kBand = std::max(1, band);
   const int nbm = (n + BMT - 1) / BMT, nbn = (n + BN - 1) / BN;
   std::vector<int2> out;
   for (int b0 = 0; b0 < nbn; b0 += kBand) {
@@ -1100,8 +1100,8 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
   // (4) H = W^H X and S = (U W)^H W over one triangle
   {
     const int uplo = ctx->opt.uplo;
-    if (ctx->tiles_n != n_g || ctx->tiles_uplo != uplo) {
-      std::vector<int2> tl = tri_tiles(n_g, uplo);
+    if (ctx->tiles_n != n_g || ctx->tiles_uplo != uplo || ctx->tiles_band != ctx->tile_band) {
+      std::vector<int2> tl = tri_tiles(n_g, uplo, ctx->tile_band);
       if (ctx->d_tiles) cudaFree(ctx->d_tiles);
       ctx->d_tiles = nullptr;
       ctx->tiles_n = -1;
@@ -1109,6 +1109,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       HSG_CUDA(ctx, cudaMemcpy(ctx->d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
       ctx->tiles_n = n_g;
       ctx->tiles_uplo = uplo;
+      ctx->tiles_band = ctx->tile_band;
       ctx->tiles_count = (long long)tl.size();
     }
     // The depth is cut into segments run as separate launches that add into
@@ -1206,7 +1207,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   std::vector<std::vector<int2>> tl(n_k);
   size_t n_tl = 0;
   for (int k = 0; k < n_k; ++k) {
-    if (n_g[k] > 0) tl[k] = tri_tiles(n_g[k], uplo);
+    if (n_g[k] > 0) tl[k] = tri_tiles(n_g[k], uplo, ctx->tile_band);
     n_tl += tl[k].size();
   }
   // ---- workspace layout
@@ -1314,7 +1315,8 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
     HSG_CUDA(ctx, cudaMemcpyAsync(d_map, hmap.data(), sizeof(CUtensorMap) * 2 * pi, cudaMemcpyHostToDevice, s));
   }
   // ---- the kernel sequence, captured once
-  std::vector<long long> key = {(long long)(uintptr_t)ws, (long long)slices, (long long)uplo, (long long)n_k};
+  std::vector<long long> key = {(long long)(uintptr_t)ws, (long long)slices, (long long)uplo, (long long)n_k,
+                                (long long)ctx->kseg_blocks, (long long)ctx->tile_band};
   for (int k = 0; k < n_k; ++k) {
     key.push_back(n_g[k]);
     key.push_back(ld[k]);

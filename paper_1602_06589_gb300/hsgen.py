@@ -47,11 +47,12 @@ class Stats(C.Structure):
                 ("ms_contract", C.c_double), ("ms_total", C.c_double), ("flops_algorithmic", C.c_double),
                 ("precision", C.c_int), ("slices", C.c_int), ("n_kpoints", C.c_int),
                 ("workspace_bytes", C.c_longlong), ("kernel_launches", C.c_longlong), ("s_form", C.c_int),
-                ("ms_s", C.c_double)]
+                ("ms_s", C.c_double), ("kseg_blocks", C.c_int), ("tile_band", C.c_int)]
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
-           "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_get_stats", "hsgen_last_error",
+           "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_autotune",
+           "hsgen_get_stats", "hsgen_last_error",
            "hsgen_destroy"]
 
 _LIB = None
@@ -86,6 +87,7 @@ def load(path: Optional[str] = None):
         lib.hsgen_coefficients_noalloc.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
         lib.hsgen_T_matrix.argtypes = [vp, C.c_int, _dp]
         lib.hsgen_depth_layout.argtypes = [vp, _ip, C.c_int]
+        lib.hsgen_autotune.argtypes = [vp, C.c_int, vp, vp, vp, C.c_longlong, vp]
         lib.hsgen_get_stats.argtypes = [vp, C.POINTER(Stats)]
         lib.hsgen_last_error.argtypes = [vp]
         lib.hsgen_last_error.restype = C.c_char_p
@@ -205,6 +207,12 @@ def hsgen_depth_layout(ctx, n_atoms: int) -> np.ndarray:
     return out
 
 
+def hsgen_autotune(ctx, n_g: int, kvec_ptr: int, H_ptr: int, S_ptr: int, ld: int, stream: int = 0):
+    st = load().hsgen_autotune(ctx, int(n_g), C.c_void_p(kvec_ptr), C.c_void_p(H_ptr), C.c_void_p(S_ptr), int(ld),
+                               C.c_void_p(stream))
+    _check(ctx, st, "hsgen_autotune")
+
+
 def hsgen_get_stats(ctx) -> dict:
     s = Stats()
     _check(ctx, load().hsgen_get_stats(ctx, C.byref(s)), "hsgen_get_stats")
@@ -281,6 +289,22 @@ class Generator:
         st = stream if stream is not None else torch.cuda.current_stream(dev)
         # column-major n_g x n_g with ld = n_g is a row-major tensor read transposed
         hsgen_build_HS(self.ctx, n_g, kv.data_ptr(), H.data_ptr(), S.data_ptr(), n_g, st.cuda_stream)
+        return H.mT, S.mT
+
+    def autotune(self, kvec, H=None, S=None, stream=None):
+        """Picks the split form's depth segment and tile band by timing builds
+        of this k-point (hsgen_autotune); returns (H, S) built with the choice."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        kv = kvec if isinstance(kvec, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(kvec))
+        kv = kv.to(dtype=torch.float64).contiguous()
+        n_g = int(kv.shape[0])
+        if H is None:
+            H = torch.zeros((n_g, n_g), dtype=torch.complex128, device=dev)
+        if S is None:
+            S = torch.zeros((n_g, n_g), dtype=torch.complex128, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        hsgen_autotune(self.ctx, n_g, kv.data_ptr(), H.data_ptr(), S.data_ptr(), n_g, st.cuda_stream)
         return H.mT, S.mT
 
     def coefficients(self, kvec, stream=None):

@@ -204,6 +204,26 @@ def test_split_config4_sampled(hs):
     sampled_check(hs, 4, n_samp=12)
 
 
+def test_split_autotune_choice_and_parity(hs):
+    """The autotuner picks a candidate schedule, keeps it for later builds and
+    its output is a correct H and S."""
+    import torch
+
+    w = make_config(2, n_g_override=3000)
+    kv = w.kvecs[0]
+    kd = torch.from_numpy(kv).cuda()
+    with hs.Generator(w.system, precision=hs.SPLIT) as g:
+        H, S = g.autotune(kd)
+        torch.cuda.synchronize()
+        st = g.stats()
+        assert st["kseg_blocks"] in (64, 96, 128, 192) and st["tile_band"] in (8, 16, 32)
+        H2, S2 = g.build(kd)
+        torch.cuda.synchronize()
+        assert torch.equal(H, H2) and torch.equal(S, S2)
+        assert g.stats()["kseg_blocks"] == st["kseg_blocks"]
+    check(w.system, kv, H.cpu().numpy(), S.cpu().numpy())
+
+
 def test_split_timeout_is_reported_and_context_recovers(hs):
     """A wait limit far below the kernel's latency makes bounded device waits
     expire; the call returns HSGEN_ETIMEOUT (no trap) and the GPU stays usable."""
