@@ -227,7 +227,8 @@ def run_batched(args, w, world, rank, local, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "strong", "vs_baseline": None, "dtype": "bf16-split/f64" if precision == hsgen.SPLIT else "f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(args.config, w), "form": args.form, "k_points_per_step": nk,
+        "config": {"workload": workload_name(args.config, w), "form": args.form, "s_form": args.s_form,
+                   "k_points_per_step": nk,
                    "parallelism": f"k-points dealt round-robin over {world} rank(s)",
                    "launch": "hsgen_build_HS_batched (grouped persistent launch, CUDA graph replay)"},
         "eff_tflops": flops_total / (ms * 1e-3) / 1e12, "gpu_launches": st["kernel_launches"] * args.steps,

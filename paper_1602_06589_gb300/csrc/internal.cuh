@@ -136,6 +136,11 @@ size_t legendre_ws_bytes(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p);
 // Writes the opt.uplo triangle of S (device, ld) from the radial factors F of
 // this k-point (F[type][t][l], as launch_radial writes them); ws holds
 // legendre_ws_bytes. Asynchronous on s (host tables are staged by the copies).
+// The two halves of legendre_S, for graph capture: the host-table uploads and
+// kernel attributes (before a capture), then the kernel launches (capturable).
+hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, void *ws, cudaStream_t s);
+hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const double2 *F,
+                             const LegendrePlan &p, void *ws, double2 *S, long long ld, cudaStream_t s);
 hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const double2 *F, const LegendrePlan &p,
                         void *ws, double2 *S, long long ld, cudaStream_t s);
 // a2: T matrix of one species (device, dpad x dpad complex, column-major).

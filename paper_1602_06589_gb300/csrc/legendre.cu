@@ -177,8 +177,6 @@ cudaError_t launch_s_lmax(int n_g, const double *K, const int *nco, const double
                           const double2 *wts, const double2 *SF, const int d[3], const int sp[3], double2 *S,
                           long long ld, int uplo, cudaStream_t s) {
   const size_t sm = sizeof(double2) * 2 * TILE * n_types * (L + 1);
-  cudaError_t e = cudaFuncSetAttribute(legendre_s_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   const long long nb = (n_g + TILE - 1) / TILE;
   const long long ntiles = nb * (nb + 1) / 2;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -222,7 +220,7 @@ bool legendre_plan(const hsgen_ctx *ctx, int n_g, const double *K, LegendrePlan 
   int lm = 0;
   for (const auto &sp : ctx->types) lm = std::max(lm, sp.lmax);
   p.lmax = lm;
-  if (sizeof(double2) * 2 * TILE * nt * (lm + 1) > 200 * 1024) return false;  // staging above shared memory
+  if (sizeof(double2) * 2 * TILE * nt * (lm + 1) > 200 * 1024) return false;  // staging above the kernel's limit
   p.ok = true;
   return true;
 }
@@ -235,22 +233,50 @@ size_t legendre_ws_bytes(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p) {
          al(sizeof(double) * 3 * na);
 }
 
-hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *K_dev, const double2 *F, const LegendrePlan &p,
-                        void *ws, double2 *S, long long ld, cudaStream_t s) {
+namespace {
+
+constexpr int kLegSmemMax = 200 * 1024;  // staging limit legendre_plan enforces
+
+template <int L>
+cudaError_t set_smem_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(legendre_s_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLegSmemMax);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+struct LegWs {
+  int *n, *lmax, *tstart;
+  double2 *sf, *w;
+  double *frac;
+};
+
+LegWs leg_ws(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p, void *ws) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const int nt = (int)ctx->types.size(), na = (int)ctx->toa.size();
+  const int nt = (int)ctx->types.size();
   char *b = (char *)ws;
-  int *d_n = (int *)b;
+  LegWs L;
+  L.n = (int *)b;
   b += al(sizeof(int) * 3 * (size_t)n_g);
-  double2 *d_sf = (double2 *)b;
+  L.sf = (double2 *)b;
   b += al(sizeof(double2) * (size_t)p.cells * nt);
-  double2 *d_w = (double2 *)b;
+  L.w = (double2 *)b;
   b += al(sizeof(double2) * nt * (kLmaxMax + 1));
-  int *d_lmax = (int *)b;
+  L.lmax = (int *)b;
   b += al(sizeof(int) * nt);
-  int *d_tstart = (int *)b;
+  L.tstart = (int *)b;
   b += al(sizeof(int) * (nt + 1));
-  double *d_frac = (double *)b;
+  L.frac = (double *)b;
+  return L;
+}
+
+}  // namespace
+
+hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, void *ws, cudaStream_t s) {
+  const int nt = (int)ctx->types.size(), na = (int)ctx->toa.size();
+  const LegWs L = leg_ws(ctx, n_g, p, ws);
   // host tables: weights (2l+1)/(4 pi) and ||u_dot_l||^2 (2l+1)/(4 pi) at stride lmax+1,
   // species l_max, species starts in the per-species atom list, fractional coordinates
   const int NLP = p.lmax + 1;
@@ -277,25 +303,44 @@ hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *K_dev, const doub
   for (int a = 0; a < na; ++a)
     for (int j = 0; j < 3; ++j)
       frac[3 * a + j] = ctx->pos[3 * a] * inv[j] + ctx->pos[3 * a + 1] * inv[3 + j] + ctx->pos[3 * a + 2] * inv[6 + j];
-  HSG_CUDA(ctx, cudaMemcpyAsync(d_n, p.nco.data(), sizeof(int) * 3 * (size_t)n_g, cudaMemcpyHostToDevice, s));
-  HSG_CUDA(ctx, cudaMemcpyAsync(d_w, w.data(), sizeof(double2) * w.size(), cudaMemcpyHostToDevice, s));
-  HSG_CUDA(ctx, cudaMemcpyAsync(d_lmax, lmax.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
-  HSG_CUDA(ctx, cudaMemcpyAsync(d_tstart, tstart.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice, s));
-  HSG_CUDA(ctx, cudaMemcpyAsync(d_frac, frac.data(), sizeof(double) * frac.size(), cudaMemcpyHostToDevice, s));
-  // pageable sources: the copies above have been staged when they return
+  // kernel attribute first (not a stream operation: must not happen inside a graph capture)
+  cudaError_t ea = cudaErrorInvalidValue;
+  switch (p.lmax) {
+#define HSG_LEG_ATTR(LM) \
+  case LM:               \
+    ea = set_smem_attr<LM>(); \
+    break;
+    HSG_LEG_ATTR(0) HSG_LEG_ATTR(1) HSG_LEG_ATTR(2) HSG_LEG_ATTR(3) HSG_LEG_ATTR(4) HSG_LEG_ATTR(5)
+    HSG_LEG_ATTR(6) HSG_LEG_ATTR(7) HSG_LEG_ATTR(8) HSG_LEG_ATTR(9) HSG_LEG_ATTR(10)
+#undef HSG_LEG_ATTR
+    default: break;
+  }
+  HSG_CUDA(ctx, ea);
+  // pageable sources: each copy has been staged when it returns
+  HSG_CUDA(ctx, cudaMemcpyAsync(L.n, p.nco.data(), sizeof(int) * 3 * (size_t)n_g, cudaMemcpyHostToDevice, s));
+  HSG_CUDA(ctx, cudaMemcpyAsync(L.w, w.data(), sizeof(double2) * w.size(), cudaMemcpyHostToDevice, s));
+  HSG_CUDA(ctx, cudaMemcpyAsync(L.lmax, lmax.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
+  HSG_CUDA(ctx, cudaMemcpyAsync(L.tstart, tstart.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice, s));
+  HSG_CUDA(ctx, cudaMemcpyAsync(L.frac, frac.data(), sizeof(double) * frac.size(), cudaMemcpyHostToDevice, s));
+  return HSGEN_OK;
+}
+
+hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *K_dev, const double2 *F, const LegendrePlan &p,
+                             void *ws, double2 *S, long long ld, cudaStream_t s) {
+  const int nt = (int)ctx->types.size();
+  const LegWs L = leg_ws(ctx, n_g, p, ws);
   {
-    const long long cells = p.cells;
-    const unsigned blocks = (unsigned)((cells + 255) / 256);
+    const unsigned blocks = (unsigned)((p.cells + 255) / 256);
     sfactor_kernel<<<blocks, 256, 0, s>>>(p.dim[0], p.dim[1], p.dim[2], p.span[0], p.span[1], p.span[2], nt,
-                                          ctx->d_atoms_by_type, d_tstart, d_frac, d_sf);
+                                          ctx->d_atoms_by_type, L.tstart, L.frac, L.sf);
     HSG_CUDA(ctx, cudaGetLastError());
     ++ctx->launches;
   }
   cudaError_t e = cudaErrorInvalidValue;
   switch (p.lmax) {
-#define HSG_LEG_CASE(L)                                                                                    \
-  case L:                                                                                                  \
-    e = launch_s_lmax<L>(n_g, K_dev, d_n, F, nt, d_lmax, d_w, d_sf, p.dim, p.span, S, ld, ctx->opt.uplo, s); \
+#define HSG_LEG_CASE(LM)                                                                                           \
+  case LM:                                                                                                         \
+    e = launch_s_lmax<LM>(n_g, K_dev, L.n, F, nt, L.lmax, L.w, L.sf, p.dim, p.span, S, ld, ctx->opt.uplo, s); \
     break;
     HSG_LEG_CASE(0) HSG_LEG_CASE(1) HSG_LEG_CASE(2) HSG_LEG_CASE(3) HSG_LEG_CASE(4) HSG_LEG_CASE(5)
     HSG_LEG_CASE(6) HSG_LEG_CASE(7) HSG_LEG_CASE(8) HSG_LEG_CASE(9) HSG_LEG_CASE(10)
@@ -305,6 +350,13 @@ hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *K_dev, const doub
   HSG_CUDA(ctx, e);
   ++ctx->launches;
   return HSGEN_OK;
+}
+
+hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *K_dev, const double2 *F, const LegendrePlan &p,
+                        void *ws, double2 *S, long long ld, cudaStream_t s) {
+  hsgen_status st = legendre_upload(ctx, n_g, p, ws, s);
+  if (st != HSGEN_OK) return st;
+  return legendre_launch(ctx, n_g, K_dev, F, p, ws, S, ld, s);
 }
 
 }  // namespace hsg

@@ -1158,7 +1158,6 @@ hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s) {
 hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec, void *const *H,
                            void *const *S, const long long *ld, cudaStream_t s) {
   if (ctx->opt.precision != HSGEN_SPLIT) return HSGEN_ENOTSUP;
-  if (ctx->opt.s_form == HSGEN_S_LEGENDRE) return HSGEN_ENOTSUP;  // k-point by k-point
   const int na = (int)ctx->toa.size();
   if (ctx->opt.atom_chunk > 0 && ctx->opt.atom_chunk < na) return HSGEN_ENOTSUP;
   if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: no system set");
@@ -1177,6 +1176,12 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
     if (st != HSGEN_OK) return st;
   }
   HSG_CUDA(ctx, cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  // S in the Legendre form: every k-point must lie on its lattice k + G
+  // (otherwise the caller's k-point loop takes over, per k-point)
+  const bool leg = ctx->opt.s_form == HSGEN_S_LEGENDRE;
+  std::vector<LegendrePlan> plans(leg ? n_k : 0);
+  for (int k = 0; k < (leg ? n_k : 0); ++k)
+    if (n_g[k] > 0 && !legendre_plan(ctx, n_g[k], kvec[k], plans[k])) return HSGEN_ENOTSUP;
   const int depth = ctx->depth;
   const long long ldk = round_up(depth, BK);
   const int nt = (int)ctx->types.size();
@@ -1230,6 +1235,9 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   const size_t o_sl = take(max_group);
   const size_t o_exp = take(sizeof(int) * 3 * (size_t)std::max<long long>(sum_ng, 1));
   const size_t o_tl = take(sizeof(int2) * std::max<size_t>(n_tl, 1));
+  std::vector<size_t> o_leg(leg ? n_k : 0);
+  for (int k = 0; k < (leg ? n_k : 0); ++k)
+    if (n_g[k] > 0) o_leg[k] = take(legendre_ws_bytes(ctx, n_g[k], plans[k]));
   const size_t n_tab = (size_t)2 * n_k * nseg;  // problems over all groups and segments
   const size_t o_prob = take(sizeof(GemmProblem) * n_tab);
   const size_t o_map = take(sizeof(CUtensorMap) * 2 * n_tab);
@@ -1296,16 +1304,18 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
         CUtensorMap ma[2], mb[2];
         const long long nt_k = (long long)tl[k].size();
         if (!hs_problems(pr2, ma, mb, n_g[k], ldk, kb0, seg, false, uplo, Wsl, Xsl, Ysl, eW, eX, eY,
-                         (double2 *)H[k], (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k, tiles, slices))
+                         (double2 *)H[k], leg ? nullptr : (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k, tiles,
+                         slices))
           return set_err(ctx, HSGEN_ECUDA, "batched: cuTensorMapEncodeTiled failed");
-        for (int j = 0; j < 2; ++j) {
+        const int np_k = leg ? 1 : 2;  // H (and S) of this k-point
+        for (int j = 0; j < np_k; ++j) {
           hprob[pi] = pr2[j];
           hmap[2 * pi] = ma[j];
           hmap[2 * pi + 1] = mb[j];
           ++pi;
           ++np;
         }
-        tiles += 2 * nt_k;
+        tiles += np_k * nt_k;
       }
       launch_tiles.push_back(tiles);
       launch_nprob.push_back(np);
@@ -1315,11 +1325,18 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
     HSG_CUDA(ctx, cudaMemcpyAsync(d_map, hmap.data(), sizeof(CUtensorMap) * 2 * pi, cudaMemcpyHostToDevice, s));
   }
   // ---- the kernel sequence, captured once
+  for (int k = 0; k < (leg ? n_k : 0); ++k)
+    if (n_g[k] > 0) {
+      hsgen_status st = legendre_upload(ctx, n_g[k], plans[k], ws + o_leg[k], s);
+      if (st != HSGEN_OK) return st;
+    }
   std::vector<long long> key = {(long long)(uintptr_t)ws, (long long)slices, (long long)uplo, (long long)n_k,
-                                (long long)ctx->kseg_blocks, (long long)ctx->tile_band};
+                                (long long)ctx->kseg_blocks, (long long)ctx->tile_band, (long long)leg};
   for (int k = 0; k < n_k; ++k) {
     key.push_back(n_g[k]);
     key.push_back(ld[k]);
+    if (leg)  // the captured launches carry each k-point's table extents
+      for (int j = 0; j < 3; ++j) key.push_back(plans[k].span[j]);
     key.push_back((long long)(uintptr_t)H[k]);
     key.push_back((long long)(uintptr_t)S[k]);
   }
@@ -1358,7 +1375,12 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           hsgen_status st2 = tapply_split(ctx, ng, 0, na, Wsl, ldk, eW, X, depth, slices, s);
           if (st2 != HSGEN_OK) return st2;
           HSG_LAUNCH(ctx, launch_slice(X, depth, depth, nullptr, slices, 3, Xsl, ldk, plane, eX, ng, s));
-          HSG_LAUNCH(ctx, launch_slice(W, depth, depth, ctx->d_urow, slices, 2, Ysl, ldk, plane, eY, ng, s));
+          if (leg) {
+            hsgen_status st3 = legendre_launch(ctx, ng, kd, F, plans[k], ws + o_leg[k], (double2 *)S[k], ld[k], s);
+            if (st3 != HSGEN_OK) return st3;
+          } else {
+            HSG_LAUNCH(ctx, launch_slice(W, depth, depth, ctx->d_urow, slices, 2, Ysl, ldk, plane, eY, ng, s));
+          }
         }
         for (int sg = 0; sg < nseg; ++sg) {
           const size_t li = gi * nseg + sg;
@@ -1402,7 +1424,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   ctx->phase_used[0] = 0;
   ctx->phase_used[1] = 0;
   ctx->phase_used[2] = 0;
-  ctx->stats.s_form = HSGEN_S_CONTRACTION;
+  ctx->stats.s_form = leg ? HSGEN_S_LEGENDRE : HSGEN_S_CONTRACTION;
   return split_check_status(ctx, s);
 }
 

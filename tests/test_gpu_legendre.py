@@ -140,6 +140,38 @@ def test_legendre_config1(hs):
     check_S(w.system, w.kvecs[0], S)
 
 
+def test_legendre_batched_graph_config3_sampled(hs):
+    """48 k-points in one graph-captured batch with S in the Legendre form:
+    sampled entries of two k-points against the oracle, and a replay (same
+    sizes, same pointers) gives the same result."""
+    import torch
+
+    w = make_config(3)
+    ks = [np.ascontiguousarray(k) for k in w.kvecs]
+    with hs.Generator(w.system, precision=hs.SPLIT, s_form=hs.S_LEGENDRE) as g:
+        Hs = [torch.zeros((k.shape[0],) * 2, dtype=torch.complex128, device="cuda") for k in ks]
+        Ss = [torch.zeros_like(h) for h in Hs]
+        args = ([k.shape[0] for k in ks], [k.ctypes.data for k in ks], [h.data_ptr() for h in Hs],
+                [s.data_ptr() for s in Ss], [k.shape[0] for k in ks])
+        hs.hsgen_build_HS_batched(g.ctx, *args)
+        torch.cuda.synchronize()
+        assert g.stats()["s_form"] == hs.S_LEGENDRE
+        first = [s.clone() for s in Ss]
+        hs.hsgen_build_HS_batched(g.ctx, *args)
+        torch.cuda.synchronize()
+        for a, b in zip(first, Ss):
+            assert torch.equal(a, b)
+        for kidx in (3, 40):
+            kv = ks[kidx]
+            n = kv.shape[0]
+            idx = np.unique(np.r_[0, np.sort(np.random.default_rng(kidx).choice(n, 10, replace=False)), n - 1])
+            r, c = np.meshgrid(idx, idx, indexing="ij")
+            sel = r <= c
+            Sg = Ss[kidx].mT[torch.from_numpy(r[sel]).cuda(), torch.from_numpy(c[sel]).cuda()].cpu().numpy()
+            _, So = oracle.HS_entries(w.system, kv, r[sel], c[sel])
+            assert np.linalg.norm(Sg - So) <= REL_F * np.linalg.norm(So)
+
+
 def test_legendre_batched_matches_single(hs):
     import torch
 
