@@ -177,9 +177,10 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
     int n1 = ty.lmax + 1;
     sp.lmax = ty.lmax;
     sp.nl = n1 * n1;
-    // depth block of one atom: 8-row aligned in both forms (the split form's
-    // X = T W reads whole 64-deep blocks through depth-shifted copies of T)
-    sp.dpad = round_up(2 * sp.nl, 8);
+    // depth block of one atom: 8-row aligned in the FP64 form; exactly 2 N_L
+    // rows in the split form (its X = T W reads whole 64-deep blocks through
+    // copies of T shifted in steps of 2 rows)
+    sp.dpad = (ctx->opt.precision == HSGEN_SPLIT) ? 2 * sp.nl : round_up(2 * sp.nl, 8);
     sp.rmt = ty.rmt;
     sp.u.assign(ty.u, ty.u + n1);
     sp.du.assign(ty.du, ty.du + n1);

@@ -19,14 +19,14 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // Species data kept by the context.
 struct Species {
-  int lmax = 0, nl = 0, dpad = 0;  // N_L = (lmax+1)^2, depth block padded to 8 rows
+  int lmax = 0, nl = 0, dpad = 0;  // N_L = (lmax+1)^2, depth block (2 N_L, padded to 8 rows in the FP64 form)
   double rmt = 0.0;
   std::vector<double> u, du, udot, dudot, wr, un2, el;
   std::vector<double> I[4];        // uu, uud, udu, udud
   std::vector<double> T_override;  // empty or (2N_L)^2 complex (interleaved), col-major
   double *d_T = nullptr;           // dpad x dpad complex col-major (ld = dpad)
   // split form: BF16 slices of T (planes re, im per slice) and column exponents.
-  // T is stored once per depth shift d = 0, 8, .., 56 (kTShifts copies), each
+  // T is stored once per depth shift d = 0, 2, .., 62 (32 copies), each
   // t_kspan deep with T's rows at [d, d + dpad) and zeros elsewhere, so that
   // X = T W of an atom whose depth offset is d mod 64 reads whole 64-deep
   // blocks of W.

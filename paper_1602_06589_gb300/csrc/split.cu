@@ -60,7 +60,8 @@ namespace hsg {
 namespace {
 
 constexpr int kMaxProb = 4;
-constexpr int kTShifts = 8;  // depth shifts 0, 8, .., 56 of the per-atom T copies
+constexpr int kTShiftStep = 2;                // atoms start on even depth rows (2 N_L rows each)
+constexpr int kTShifts = 64 / kTShiftStep;    // depth shifts 0, 2, .., 62 of the per-atom T copies
 // BM: rows of A per CTA (one TMA box); BMT: rows of a tile (a CTA pair)
 constexpr int BM = 128, BMT = 256, BN = 64, BK = 64;
 // A pipeline stage holds KPS 64-deep k-blocks: large stages keep the fixed
@@ -321,14 +322,14 @@ __device__ __forceinline__ Tile decode_tile(const GemmParams &P, long long t) {
     int rem = (int)(lt % per);
     bi = rem % pr.nbm;
     bj = rem / pr.nbm;
-    koff = pr.off[pr.atoms[b]] - pr.row_base;  // a multiple of 8
+    koff = pr.off[pr.atoms[b]] - pr.row_base;  // a multiple of kTShiftStep
   }
   ti.m0 = bi * BMT;
   ti.n0 = bj * BN;
   // B starts at the 64-deep block holding the atom's first row; A is the copy
   // of T shifted down by the rest (zero rows elsewhere)
   ti.b_k0 = koff & ~(BK - 1);
-  ti.a_p0 = ((koff & (BK - 1)) >> 3) * pr.a_shift_planes;
+  ti.a_p0 = ((koff & (BK - 1)) / kTShiftStep) * pr.a_shift_planes;
   ti.c_row0 = koff;
   ti.nkb = (pr.K + BK - 1) / BK;
   return ti;
@@ -1039,13 +1040,13 @@ hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
     sp.d_Tsl = nullptr;
     sp.d_Texp = nullptr;
     // shifted copies of T (FP64, kspan x dpad each), then their slices
-    sp.t_kspan = round_up(sp.dpad + BK - 8, BK);
+    sp.t_kspan = round_up(sp.dpad + BK - kTShiftStep, BK);
     const size_t span = (size_t)sp.t_kspan * sp.dpad;
     double2 *Tsh = nullptr;
     HSG_CUDA(ctx, cudaMalloc(&Tsh, sizeof(double2) * span * kTShifts));
     HSG_CUDA(ctx, cudaMemset(Tsh, 0, sizeof(double2) * span * kTShifts));
     for (int d = 0; d < kTShifts; ++d)
-      HSG_CUDA(ctx, cudaMemcpy2D(Tsh + d * span + 8 * d, sizeof(double2) * sp.t_kspan, sp.d_T,
+      HSG_CUDA(ctx, cudaMemcpy2D(Tsh + d * span + kTShiftStep * d, sizeof(double2) * sp.t_kspan, sp.d_T,
                                  sizeof(double2) * sp.dpad, sizeof(double2) * sp.dpad, sp.dpad,
                                  cudaMemcpyDeviceToDevice));
     HSG_CUDA(ctx, cudaMalloc(&sp.d_Tsl, span * 2 * slices * kTShifts * sizeof(__nv_bfloat16)));
