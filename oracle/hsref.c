@@ -203,13 +203,16 @@ int hsref_T(const hsref_type *ty, double *T) {
   }
   memset(T, 0, sizeof(double) * 2 * (size_t)n * n);
   const double *Ixy[2][2] = {{ty->I_uu, ty->I_uud}, {ty->I_udu, ty->I_udud}}; /* [x][y] */
+  /* Sec. 3.1 (Fig. Tmat_structure): the non-spherical (Gaunt) part is dense for
+   * l, l' <= l_nonsph only; the spherical diagonal below runs to lmax */
+  const int lns = ty->lmax_nonsph < lmax ? ty->lmax_nonsph : lmax;
   for (int lp = 0; lp <= lmax; ++lp)
     for (int mp = -lp; mp <= lp; ++mp)
       for (int l = 0; l <= lmax; ++l)
         for (int m = -l; m <= l; ++m) {
           int Lp = lp * lp + lp + mp, L = l * l + l + m, mpp = mp - m;
           double acc[2][2] = {{0, 0}, {0, 0}};
-          for (int lpp = abs(l - lp); lpp <= l + lp; ++lpp) {
+          for (int lpp = abs(l - lp); lpp <= l + lp && l <= lns && lp <= lns; ++lpp) {
             if ((l + lp + lpp) & 1) continue;
             if (abs(mpp) > lpp) continue;
             double g = hsref_gaunt(l, m, lp, mp, lpp, mpp) * cpot(mpp);

@@ -34,6 +34,9 @@ typedef struct {
   const double *e_l;                   /* [lmax+1]                          */
   const double *I_uu, *I_uud, *I_udu, *I_udud; /* [lmax+1][lmax+1][2lmax+1] */
   const double *T_override; /* NULL, or (2N_L)^2 complex, column-major      */
+  int lmax_nonsph;          /* l_nonsph (Sec. 3.1, Fig. Tmat_structure): the */
+                            /* Gaunt sum enters T only for l, l' <= l_nonsph */
+                            /* (l_nonsph >= lmax: everywhere)                */
 } hsref_type;
 
 typedef struct {

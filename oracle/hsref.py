@@ -26,7 +26,7 @@ class _Type(C.Structure):
                 ("u", _dp), ("du", _dp), ("udot", _dp), ("dudot", _dp),
                 ("udot_norm2", _dp), ("e_l", _dp),
                 ("I_uu", _dp), ("I_uud", _dp), ("I_udu", _dp), ("I_udud", _dp),
-                ("T_override", _dp)]
+                ("T_override", _dp), ("lmax_nonsph", C.c_int)]
 
 
 class _System(C.Structure):
@@ -96,6 +96,8 @@ class _Marshal:
             self.keep.extend(arrs.values())
             types[i].lmax = int(t.lmax)
             types[i].rmt = float(t.rmt)
+            lns = getattr(t, "lmax_nonsph", None)
+            types[i].lmax_nonsph = int(t.lmax) if lns is None else int(lns)
             for k, v in arrs.items():
                 setattr(types[i], k, _d(v))
             if t.T_override is not None:

@@ -60,6 +60,8 @@ MUTATIONS = {
     "Wronskian sign": (
         "double W = ty->udot[l] * ty->du[l] - ty->u[l] * ty->dudot[l];",
         "double W = ty->u[l] * ty->dudot[l] - ty->udot[l] * ty->du[l];"),
+    "l_nonsph cutoff on one index only": (
+        "lpp <= l + lp && l <= lns && lp <= lns; ++lpp", "lpp <= l + lp && l <= lns; ++lpp"),
     "conjugate on the wrong side of the dot": (
         "sr += pr * qr + pi * qi;\n      si += pr * qi - pi * qr;",
         "sr += pr * qr + pi * qi;\n      si += pi * qr - pr * qi;"),
@@ -75,6 +77,7 @@ PINS = [
     lambda: P.test_S_single_plane_wave(),
     lambda: P.test_H_spherical_only_closed_form(),
     lambda: P.test_H_quadrature_form("small"),
+    lambda: P.test_H_quadrature_form("small-lns"),
     lambda: P.test_H_rank_one_T(),
     lambda: P.test_hermitian_psd_and_brute_force_c0(),
     lambda: P.test_invariances(),

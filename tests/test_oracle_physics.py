@@ -207,16 +207,23 @@ def _sphere_grid(nth, nph):
     return pts, W.reshape(-1)
 
 
-@pytest.mark.parametrize("cfg", ["c0", "small"])
+@pytest.mark.parametrize("cfg", ["c0", "small", "small-lns"])
 def test_H_quadrature_form(cfg):
     """Non-spherical H from the angular integral of Phi^{x*}_{l',t'} V_{l''} Phi^y_{l,t}
-    on an exact product grid (no Gaunt table), plus the spherical Legendre part."""
+    on an exact product grid (no Gaunt table), plus the spherical Legendre part.
+    "small-lns": l_nonsph = 1 (Sec. 3.1, Fig. Tmat_structure): the non-spherical
+    integral only couples l, l' <= 1, the spherical part runs to l_max."""
+    lns = None
     if cfg == "c0":
         w = make_config(0)
         sysm, kv = w.system, w.kvecs[0][::10]
     else:
         sysm = small_system(lmax=3, n_atoms=2, seed=13)
         kv = kpoint_list(sysm.lattice, (0.05, 0.3, -0.2), 60)[::4]
+        if cfg == "small-lns":
+            lns = 1
+            for ty in sysm.types:
+                ty.lmax_nonsph = lns
     n = kv.shape[0]
     H, _ = oracle.build_HS(sysm, kv, full=True)
     ref = legendre_form(sysm, kv, h_sph_diag)
@@ -241,9 +248,10 @@ def test_H_quadrature_form(cfg):
                 c = 1.0 if m2 >= 0 else (-1.0) ** m2
                 V[l2] += c * Y[:, l2 * l2 + l2 + m2]
         Ixy = {("A", "A"): ty.I_uu, ("A", "B"): ty.I_uud, ("B", "A"): ty.I_udu, ("B", "B"): ty.I_udud}
+        lcut = lm if lns is None else min(lns, lm)
         for (x, y), I in Ixy.items():
-            for l in range(lm + 1):
-                for lp in range(lm + 1):
+            for l in range(lcut + 1):
+                for lp in range(lcut + 1):
                     for l2 in range(2 * lm + 1):
                         if I[l, lp, l2] == 0.0:
                             continue
@@ -361,6 +369,31 @@ def test_T_hermitian_and_structure():
         nl = ty.nl
         assert np.max(np.abs(T - T.conj().T)) < 1e-14 * np.max(np.abs(T))
         assert np.max(np.abs(T[nl:, :nl] - T[:nl, nl:].conj().T)) < 1e-14  # T^BA = (T^AB)^H
+
+
+def test_T_nonsph_block_structure():
+    """l_nonsph < l_max (Fig. Tmat_structure): inside the dense block T equals the
+    full T; outside it only the spherical diagonal of App. A.2 remains (E_l,
+    E_l ||u_dot_l||^2, and 1/2 on AB and BA, reading R1)."""
+    sysm = small_system(lmax=4, n_atoms=2, seed=23)
+    for ty in sysm.types:
+        full = oracle.T_matrix(ty)
+        for lns in range(0, ty.lmax):
+            t2 = copy.deepcopy(ty)
+            t2.lmax_nonsph = lns
+            T = oracle.T_matrix(t2)
+            nl = ty.nl
+            lvec = np.repeat(np.arange(ty.lmax + 1), 2 * np.arange(ty.lmax + 1) + 1)
+            inner = np.tile(lvec <= lns, 2)
+            blk = np.outer(inner, inner)
+            assert np.array_equal(T[blk], full[blk])
+            sph = np.zeros_like(full)
+            for L, l in enumerate(lvec):
+                sph[L, L] = ty.e_l[l]
+                sph[nl + L, nl + L] = ty.e_l[l] * ty.udot_norm2[l]
+                sph[L, nl + L] = sph[nl + L, L] = 0.5
+            assert np.max(np.abs(T[~blk] - sph[~blk])) < 1e-15
+            assert np.max(np.abs(T - T.conj().T)) < 1e-14 * np.max(np.abs(T))
 
 
 def test_compensated_vs_plain():

@@ -58,6 +58,9 @@ class AtomType:
     I_udu: np.ndarray
     I_udud: np.ndarray
     T_override: Optional[np.ndarray] = None  # complex (2N_L, 2N_L) or None
+    # l_nonsph: the non-spherical (Gaunt) part of T is dense for l, l' <= it;
+    # None means l_max (Sec. 3.1, Fig. Tmat_structure)
+    lmax_nonsph: Optional[int] = None
 
     @property
     def nl(self) -> int:
