@@ -94,6 +94,15 @@ typedef struct {
   const double *T_override;         /* NULL, or (2N_L)^2 complex, column-major */
                                     /* Hermitian T used instead of Eq.         */
                                     /* t_matrices (rows/cols: A then B)        */
+  int lmax_nonsph;                  /* l_nonsph (Sec. 3.1, Fig. Tmat_structure):*/
+                                    /* the Gaunt part of T only for l, l' <=   */
+                                    /* it, the spherical diagonal to lmax;     */
+                                    /* < 0 or >= lmax: lmax. With s_form       */
+                                    /* HSGEN_S_LEGENDRE the contraction then   */
+                                    /* covers l <= l_nonsph only and H's       */
+                                    /* spherical tail is added in the Legendre */
+                                    /* form (every K_t must be on one lattice  */
+                                    /* k + G: HSGEN_ENOTSUP otherwise)         */
 } hsgen_type;
 
 typedef struct {
@@ -174,7 +183,8 @@ hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, voi
  * read is written earlier in the same call. */
 hsgen_status hsgen_coefficients_noalloc(hsgen_ctx *ctx, int n_g, const double *kvec, void *W, long long ldw,
                                         void *cuda_stream);
-/* T of species `type` (a2) copied into T (host, (2N_L)^2 complex, column-major). */
+/* T of species `type` (a2) copied into T (host, (2N_L)^2 complex, column-major),
+ * with the l_nonsph structure of Fig. Tmat_structure. */
 hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T);
 /* Row offsets of the atoms in the depth of W (offsets[n_atoms+1], host); the
  * block of atom a is offsets[a] .. offsets[a] + 2 N_La (A rows, then B rows),

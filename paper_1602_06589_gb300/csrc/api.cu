@@ -177,10 +177,16 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
     int n1 = ty.lmax + 1;
     sp.lmax = ty.lmax;
     sp.nl = n1 * n1;
+    sp.lns = (ty.lmax_nonsph < 0 || ty.lmax_nonsph >= ty.lmax) ? ty.lmax : ty.lmax_nonsph;
+    // the contraction covers l <= lns only when S (and H's spherical tail) come
+    // from the Legendre form; a caller-supplied T is taken as it is
+    sp.lc = (ctx->opt.s_form == HSGEN_S_LEGENDRE && !ty.T_override) ? sp.lns : sp.lmax;
+    if (ty.T_override) sp.lns = sp.lmax;
+    sp.nlc = (sp.lc + 1) * (sp.lc + 1);
     // depth block of one atom: 8-row aligned in the FP64 form; exactly 2 N_L
     // rows in the split form (its X = T W reads whole 64-deep blocks through
     // copies of T shifted in steps of 2 rows)
-    sp.dpad = (ctx->opt.precision == HSGEN_SPLIT) ? 2 * sp.nl : round_up(2 * sp.nl, 8);
+    sp.dpad = (ctx->opt.precision == HSGEN_SPLIT) ? 2 * sp.nlc : round_up(2 * sp.nlc, 8);
     sp.rmt = ty.rmt;
     sp.u.assign(ty.u, ty.u + n1);
     sp.du.assign(ty.du, ty.du + n1);
@@ -238,11 +244,11 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
   std::vector<double> urow(ctx->depth, 0.0);
   for (int a = 0; a < n_atoms; ++a) {
     const Species &sp = ctx->types[ctx->toa[a]];
-    for (int l = 0; l <= sp.lmax; ++l)
+    for (int l = 0; l <= sp.lc; ++l)
       for (int m = -l; m <= l; ++m) {
         int L = l * l + l + m;
         urow[ctx->off[a] + L] = 1.0;
-        urow[ctx->off[a] + sp.nl + L] = sp.un2[l];
+        urow[ctx->off[a] + sp.nlc + L] = sp.un2[l];
       }
   }
   // atom lists grouped by species
@@ -323,10 +329,34 @@ hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T) {
   if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "T_matrix: no system set");
   if (type < 0 || type >= (int)ctx->types.size()) return set_err(ctx, HSGEN_EINVAL, "T_matrix: bad type");
   const Species &sp = ctx->types[type];
-  int n = 2 * sp.nl;
+  const int n = 2 * sp.nl, nc = 2 * sp.nlc;
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
-  HSG_CUDA(ctx, cudaMemcpy2D(T, sizeof(double2) * n, sp.d_T, sizeof(double2) * sp.dpad, sizeof(double2) * n, n,
-                             cudaMemcpyDeviceToHost));
+  if (nc == n) {
+    HSG_CUDA(ctx, cudaMemcpy2D(T, sizeof(double2) * n, sp.d_T, sizeof(double2) * sp.dpad, sizeof(double2) * n, n,
+                               cudaMemcpyDeviceToHost));
+    return HSGEN_OK;
+  }
+  // contraction block (l <= lc, A then B rows) placed into the full matrix,
+  // plus the spherical diagonal of the rows beyond it (App. A.2, reading R1)
+  std::vector<double2> blk((size_t)nc * nc);
+  HSG_CUDA(ctx, cudaMemcpy2D(blk.data(), sizeof(double2) * nc, sp.d_T, sizeof(double2) * sp.dpad,
+                             sizeof(double2) * nc, nc, cudaMemcpyDeviceToHost));
+  std::memset(T, 0, sizeof(double) * 2 * (size_t)n * n);
+  auto full_row = [&](int r) { return r < sp.nlc ? r : sp.nl + (r - sp.nlc); };
+  for (int c = 0; c < nc; ++c)
+    for (int r = 0; r < nc; ++r) {
+      const size_t o = 2 * ((size_t)full_row(r) + (size_t)full_row(c) * n);
+      T[o] = blk[r + (size_t)c * nc].x;
+      T[o + 1] = blk[r + (size_t)c * nc].y;
+    }
+  for (int l = sp.lc + 1; l <= sp.lmax; ++l)
+    for (int m = -l; m <= l; ++m) {
+      const int L = l * l + l + m, B = sp.nl + L;
+      T[2 * (L + (size_t)L * n)] = sp.el[l];
+      T[2 * (B + (size_t)B * n)] = sp.el[l] * sp.un2[l];
+      T[2 * (L + (size_t)B * n)] = 0.5;
+      T[2 * (B + (size_t)L * n)] = 0.5;
+    }
   return HSGEN_OK;
 }
 
@@ -400,7 +430,7 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
       while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
       if (hi == lo) continue;
       const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
-      HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, n_g, job.kvec_dev, F + (size_t)t * n_g * kRadStride,
+      HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lc, n_g, job.kvec_dev, F + (size_t)t * n_g * kRadStride,
                                           d_atoms, hi - lo, ctx->d_pos, ctx->d_rot, ctx->d_off, row_base,
                                           ctx->types[t].dpad, W, L.ldw, s));
     }
@@ -429,7 +459,7 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
   if (job.leg) {
-    hsgen_status st = legendre_S(ctx, n_g, job.kvec_dev, F, *job.leg, ctx->ws_leg.ptr, job.S, job.ld, s);
+    hsgen_status st = legendre_S(ctx, n_g, job.kvec_dev, F, *job.leg, ctx->ws_leg.ptr, job.S, job.H, job.ld, s);
     if (st != HSGEN_OK) return st;
     if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
   }
@@ -495,7 +525,7 @@ hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, voi
   for (int t = 0; t < (int)ctx->types.size(); ++t) {
     int n = (int)ctx->atoms_of_type[t].size();
     if (!n) continue;
-    HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, n_g, kd, F + (size_t)t * n_g * kRadStride,
+    HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lc, n_g, kd, F + (size_t)t * n_g * kRadStride,
                                       ctx->d_atoms_by_type + ctx->atoms_by_type_start[t], n, ctx->d_pos, ctx->d_rot,
                                       ctx->d_off, 0, ctx->types[t].dpad, (double2 *)W, ldw, s));
   }
@@ -561,6 +591,11 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
       st = ensure_ws(ctx, ctx->ws_leg, legendre_ws_bytes(ctx, n_g, plan));
       if (st != HSGEN_OK) return st;
       job.leg = &plan;
+    } else {
+      for (const auto &sp : ctx->types)
+        if (sp.lc < sp.lmax)
+          return set_err(ctx, HSGEN_ENOTSUP,
+                         "build_HS: l_nonsph < l_max with the Legendre form needs every K_t on one lattice k + G");
     }
   }
   ctx->launches = 0;

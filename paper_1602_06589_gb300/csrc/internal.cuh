@@ -19,12 +19,18 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // Species data kept by the context.
 struct Species {
-  int lmax = 0, nl = 0, dpad = 0;  // N_L = (lmax+1)^2, depth block (2 N_L, padded to 8 rows in the FP64 form)
+  int lmax = 0, nl = 0;            // l_max, N_L = (lmax+1)^2
+  int lns = 0;                     // l_nonsph: the Gaunt part of T is dense for l, l' <= lns
+  // The contraction's view of the species: l_max lc and N_L nlc = (lc+1)^2 of
+  // the coefficient rows it multiplies (lc = lns when S is in the Legendre form,
+  // which then also adds H's spherical tail lns < l <= lmax; lc = lmax otherwise),
+  // its depth block dpad (2 nlc rows; padded to 8 in the FP64 form) and T (d_T).
+  int lc = 0, nlc = 0, dpad = 0;
   double rmt = 0.0;
   std::vector<double> u, du, udot, dudot, wr, un2, el;
   std::vector<double> I[4];        // uu, uud, udu, udud
   std::vector<double> T_override;  // empty or (2N_L)^2 complex (interleaved), col-major
-  double *d_T = nullptr;           // dpad x dpad complex col-major (ld = dpad)
+  double *d_T = nullptr;           // contraction block of T: dpad x dpad complex col-major (ld = dpad)
   // split form: BF16 slices of T (planes re, im per slice) and column exponents.
   // T is stored once per depth shift d = 0, 2, .., 62 (32 copies), each
   // t_kspan deep with T's rows at [d, d + dpad) and zeros elsewhere, so that
@@ -130,19 +136,21 @@ struct LegendrePlan {
   int span[3] = {0, 0, 0}, dim[3] = {1, 1, 1};
   long long cells = 1;
   int lmax = 0;
+  bool tail = false;  // some species' contraction stops below its l_max: add H's spherical tail
 };
 bool legendre_plan(const hsgen_ctx *ctx, int n_g, const double *kvec_host, LegendrePlan &p);
 size_t legendre_ws_bytes(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p);
 // Writes the opt.uplo triangle of S (device, ld) from the radial factors F of
-// this k-point (F[type][t][l], as launch_radial writes them); ws holds
-// legendre_ws_bytes. Asynchronous on s (host tables are staged by the copies).
+// this k-point (F[type][t][l], as launch_radial writes them) and, when the plan
+// has a tail, adds H's spherical rows beyond each species' contraction into H;
+// ws holds legendre_ws_bytes. Asynchronous on s (host tables are staged by the copies).
 // The two halves of legendre_S, for graph capture: the host-table uploads and
 // kernel attributes (before a capture), then the kernel launches (capturable).
 hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, void *ws, cudaStream_t s);
 hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const double2 *F,
-                             const LegendrePlan &p, void *ws, double2 *S, long long ld, cudaStream_t s);
+                             const LegendrePlan &p, void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s);
 hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const double2 *F, const LegendrePlan &p,
-                        void *ws, double2 *S, long long ld, cudaStream_t s);
+                        void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s);
 // a2: T matrix of one species (device, dpad x dpad complex, column-major).
 cudaError_t launch_tmatrix(const Species &sp, double2 *d_T, double *scratch, cudaStream_t s);
 // Recurrence tables in constant memory (called once per device).

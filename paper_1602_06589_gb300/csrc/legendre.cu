@@ -14,6 +14,13 @@
 // plane waves, so the atom sum depends on t, t' only through dn and is
 // tabulated once per k-point over the box of differences. Per entry this is
 // ~170 FP64 operations instead of 16 sum_a N_L flops of the contraction.
+//
+// With l_nonsph < l_max (Sec. 3.1, Fig. Tmat_structure) T is diagonal in L
+// for l > l_nonsph, with the spherical 2 x 2 block [[E_l, 1/2], [1/2,
+// E_l ||u_dot_l||^2]] (reading R1) coupling A and B of the same L; the same
+// m-sum turns H's part from those rows into
+//   H_tail = sum_tau SF_tau sum_{l_c < l <= l_max} (2l+1)/(4 pi) P_l sum_{x,y} T^{xy}_l F_x(t) F_y(t'),
+// which the same pass adds into H (the contraction covers l <= l_c).
 #include "internal.cuh"
 
 #include <algorithm>
@@ -57,17 +64,21 @@ __global__ void sfactor_kernel(int d1, int d2, int d3, int s1, int s2, int s3, i
   }
 }
 
-// One CTA per TILE x TILE tile of the chosen triangle.
-template <int LMAX>
+// One CTA per TILE x TILE tile of the chosen triangle. TAIL: also add H's
+// spherical tail (htab[(tau, l)] = (T^AA, T^AB), (T^BA, T^BB) times (2l+1)/(4 pi),
+// zero for l <= l_c) into H.
+template <int LMAX, bool TAIL>
 __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
     int n_g, const double *__restrict__ K, const int *__restrict__ nco, const double2 *__restrict__ F, int n_types,
-    const int *__restrict__ lmax_of, const double2 *__restrict__ wts, const double2 *__restrict__ SF, int d2, int d3,
-    int s1, int s2, int s3, double2 *__restrict__ S, long long ld, int uplo) {
+    const int *__restrict__ lmax_of, const double2 *__restrict__ wts, const double2 *__restrict__ htab,
+    const double2 *__restrict__ SF, int d2, int d3, int s1, int s2, int s3, double2 *__restrict__ S,
+    double2 *__restrict__ H, long long ld, int uplo) {
   constexpr int NLP = LMAX + 1;
   extern __shared__ double2 smem[];
   const int nlf = n_types * NLP;
   double2 *rowF = smem;              // [TILE][n_types][NLP], scaled by the weights
   double2 *colF = smem + TILE * nlf; // [TILE][n_types][NLP]
+  double2 *rowH = colF + TILE * nlf; // TAIL: [TILE][n_types][NLP], transformed by the tail's T blocks
   __shared__ double rK[TILE][3], cK[TILE][3];
   __shared__ int rN[TILE][3], cN[TILE][3];
 
@@ -81,18 +92,23 @@ __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
 
   for (int i = threadIdx.x; i < TILE * nlf; i += LTHREADS) {
     const int tt = i / nlf, rem = i - tt * nlf, ty = rem / NLP, l = rem - ty * NLP;
-    double2 fr = make_double2(0.0, 0.0), fc = make_double2(0.0, 0.0);
+    double2 fr = make_double2(0.0, 0.0), fc = make_double2(0.0, 0.0), fh = make_double2(0.0, 0.0);
     if (l <= lmax_of[ty]) {  // entries above a species' l_max are never read from F
       const double2 w = wts[ty * NLP + l];
       const int tr = r0 + tt, tc = c0 + tt;
       if (tr < n_g) {
         const double2 f = F[((size_t)ty * n_g + tr) * kRadStride + l];
         fr = make_double2(f.x * w.x, f.y * w.y);
+        if (TAIL) {  // (sum_x T^{xA} F_x, sum_x T^{xB} F_x)
+          const double2 ha = htab[2 * (ty * NLP + l)], hb = htab[2 * (ty * NLP + l) + 1];
+          fh = make_double2(fma(ha.x, f.x, hb.x * f.y), fma(ha.y, f.x, hb.y * f.y));
+        }
       }
       if (tc < n_g) fc = F[((size_t)ty * n_g + tc) * kRadStride + l];
     }
     rowF[i] = fr;
     colF[i] = fc;
+    if (TAIL) rowH[i] = fh;
   }
   if (threadIdx.x < 2 * TILE) {
     const int side = threadIdx.x / TILE, tt = threadIdx.x % TILE;
@@ -140,16 +156,21 @@ __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
       P[j][l] = fma(c_bonnet[l].x * ct, P[j][l - 1], -c_bonnet[l].y * P[j][l - 2]);
   }
   double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  double2 acch[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
   for (int ty = 0; ty < n_types; ++ty) {
-    double g[2] = {0.0, 0.0};
+    double g[2] = {0.0, 0.0}, gh[2] = {0.0, 0.0};
     const double2 *rf = rowF + tr * nlf + ty * NLP;
+    const double2 *rh = rowH + tr * nlf + ty * NLP;
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
       const double2 a = rf[l];
+      double2 ah;
+      if (TAIL) ah = rh[l];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const double2 b = colF[(cg + 16 * j) * nlf + ty * NLP + l];
         g[j] = fma(P[j][l], fma(a.x, b.x, a.y * b.y), g[j]);
+        if (TAIL) gh[j] = fma(P[j][l], fma(ah.x, b.x, ah.y * b.y), gh[j]);
       }
     }
 #pragma unroll
@@ -160,6 +181,10 @@ __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
       const double2 sf = SF[idx * n_types + ty];
       acc[j].x = fma(g[j], sf.x, acc[j].x);
       acc[j].y = fma(g[j], sf.y, acc[j].y);
+      if (TAIL) {
+        acch[j].x = fma(gh[j], sf.x, acch[j].x);
+        acch[j].y = fma(gh[j], sf.y, acch[j].y);
+      }
     }
   }
 #pragma unroll
@@ -169,19 +194,31 @@ __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
     double2 v = acc[j];
     if (row == col[j]) v.y = 0.0;
     S[(size_t)col[j] * ld + row] = v;
+    if (TAIL) {
+      double2 h = H[(size_t)col[j] * ld + row];
+      h.x += acch[j].x;
+      h.y = (row == col[j]) ? 0.0 : h.y + acch[j].y;
+      H[(size_t)col[j] * ld + row] = h;
+    }
   }
 }
 
 template <int L>
 cudaError_t launch_s_lmax(int n_g, const double *K, const int *nco, const double2 *F, int n_types, const int *lmax_of,
-                          const double2 *wts, const double2 *SF, const int d[3], const int sp[3], double2 *S,
-                          long long ld, int uplo, cudaStream_t s) {
-  const size_t sm = sizeof(double2) * 2 * TILE * n_types * (L + 1);
+                          const double2 *wts, const double2 *htab, const double2 *SF, const int d[3], const int sp[3],
+                          double2 *S, double2 *H, long long ld, int uplo, cudaStream_t s) {
   const long long nb = (n_g + TILE - 1) / TILE;
   const long long ntiles = nb * (nb + 1) / 2;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  legendre_s_kernel<L><<<(unsigned)ntiles, LTHREADS, sm, s>>>(n_g, K, nco, F, n_types, lmax_of, wts, SF, d[1], d[2],
-                                                              sp[0], sp[1], sp[2], S, ld, uplo);
+  if (H) {
+    const size_t sm = sizeof(double2) * 3 * TILE * n_types * (L + 1);
+    legendre_s_kernel<L, true><<<(unsigned)ntiles, LTHREADS, sm, s>>>(
+        n_g, K, nco, F, n_types, lmax_of, wts, htab, SF, d[1], d[2], sp[0], sp[1], sp[2], S, H, ld, uplo);
+  } else {
+    const size_t sm = sizeof(double2) * 2 * TILE * n_types * (L + 1);
+    legendre_s_kernel<L, false><<<(unsigned)ntiles, LTHREADS, sm, s>>>(
+        n_g, K, nco, F, n_types, lmax_of, wts, htab, SF, d[1], d[2], sp[0], sp[1], sp[2], S, H, ld, uplo);
+  }
   return cudaGetLastError();
 }
 
@@ -218,9 +255,14 @@ bool legendre_plan(const hsgen_ctx *ctx, int n_g, const double *K, LegendrePlan 
   const size_t nt = ctx->types.size();
   if ((double)cells * nt * sizeof(double2) > 1.0 * (1ull << 30)) return false;  // table above 1 GiB
   int lm = 0;
-  for (const auto &sp : ctx->types) lm = std::max(lm, sp.lmax);
+  p.tail = false;
+  for (const auto &sp : ctx->types) {
+    lm = std::max(lm, sp.lmax);
+    p.tail = p.tail || sp.lc < sp.lmax;
+  }
   p.lmax = lm;
-  if (sizeof(double2) * 2 * TILE * nt * (lm + 1) > 200 * 1024) return false;  // staging above the kernel's limit
+  if (sizeof(double2) * (p.tail ? 3 : 2) * TILE * nt * (lm + 1) > 200 * 1024)
+    return false;  // staging above the kernel's limit
   p.ok = true;
   return true;
 }
@@ -228,9 +270,10 @@ bool legendre_plan(const hsgen_ctx *ctx, int n_g, const double *K, LegendrePlan 
 size_t legendre_ws_bytes(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t nt = ctx->types.size(), na = ctx->toa.size();
+  // the regions leg_ws() carves, in its order
   return al(sizeof(int) * 3 * (size_t)n_g) + al(sizeof(double2) * (size_t)p.cells * nt) +
-         al(sizeof(double2) * nt * (kLmaxMax + 1)) + al(sizeof(int) * nt) + al(sizeof(int) * (nt + 1)) +
-         al(sizeof(double) * 3 * na);
+         al(sizeof(double2) * nt * (kLmaxMax + 1)) + al(sizeof(double2) * 2 * nt * (kLmaxMax + 1)) +
+         al(sizeof(int) * nt) + al(sizeof(int) * (nt + 1)) + al(sizeof(double) * 3 * na);
 }
 
 namespace {
@@ -242,14 +285,16 @@ cudaError_t set_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e =
-      cudaFuncSetAttribute(legendre_s_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLegSmemMax);
+      cudaFuncSetAttribute(legendre_s_kernel<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLegSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(legendre_s_kernel<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLegSmemMax);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
 struct LegWs {
   int *n, *lmax, *tstart;
-  double2 *sf, *w;
+  double2 *sf, *w, *h;
   double *frac;
 };
 
@@ -264,6 +309,8 @@ LegWs leg_ws(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p, void *ws) {
   b += al(sizeof(double2) * (size_t)p.cells * nt);
   L.w = (double2 *)b;
   b += al(sizeof(double2) * nt * (kLmaxMax + 1));
+  L.h = (double2 *)b;
+  b += al(sizeof(double2) * 2 * nt * (kLmaxMax + 1));
   L.lmax = (int *)b;
   b += al(sizeof(int) * nt);
   L.tstart = (int *)b;
@@ -281,6 +328,7 @@ hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, voi
   // species l_max, species starts in the per-species atom list, fractional coordinates
   const int NLP = p.lmax + 1;
   std::vector<double2> w((size_t)nt * NLP, make_double2(0.0, 0.0));
+  std::vector<double2> h(2 * (size_t)nt * NLP, make_double2(0.0, 0.0));
   std::vector<int> lmax(nt), tstart(ctx->atoms_by_type_start.begin(), ctx->atoms_by_type_start.end());
   for (int t = 0; t < nt; ++t) {
     const Species &sp = ctx->types[t];
@@ -288,6 +336,10 @@ hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, voi
     for (int l = 0; l <= sp.lmax; ++l) {
       const double c = (2.0 * l + 1.0) * kInv4Pi;
       w[(size_t)t * NLP + l] = make_double2(c, c * sp.un2[l]);
+      if (l > sp.lc) {  // H's spherical tail: (T^AA, T^AB), (T^BA, T^BB) of l, times c
+        h[2 * ((size_t)t * NLP + l)] = make_double2(c * sp.el[l], c * 0.5);
+        h[2 * ((size_t)t * NLP + l) + 1] = make_double2(c * 0.5, c * sp.el[l] * sp.un2[l]);
+      }
     }
   }
   // fractional coordinates: x = sum_j f_j a_j, i.e. f = x A^{-1} with A's rows a_j
@@ -319,6 +371,7 @@ hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, voi
   // pageable sources: each copy has been staged when it returns
   HSG_CUDA(ctx, cudaMemcpyAsync(L.n, p.nco.data(), sizeof(int) * 3 * (size_t)n_g, cudaMemcpyHostToDevice, s));
   HSG_CUDA(ctx, cudaMemcpyAsync(L.w, w.data(), sizeof(double2) * w.size(), cudaMemcpyHostToDevice, s));
+  HSG_CUDA(ctx, cudaMemcpyAsync(L.h, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice, s));
   HSG_CUDA(ctx, cudaMemcpyAsync(L.lmax, lmax.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
   HSG_CUDA(ctx, cudaMemcpyAsync(L.tstart, tstart.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice, s));
   HSG_CUDA(ctx, cudaMemcpyAsync(L.frac, frac.data(), sizeof(double) * frac.size(), cudaMemcpyHostToDevice, s));
@@ -326,7 +379,7 @@ hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, voi
 }
 
 hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *K_dev, const double2 *F, const LegendrePlan &p,
-                             void *ws, double2 *S, long long ld, cudaStream_t s) {
+                             void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s) {
   const int nt = (int)ctx->types.size();
   const LegWs L = leg_ws(ctx, n_g, p, ws);
   {
@@ -340,7 +393,8 @@ hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *K_dev, const
   switch (p.lmax) {
 #define HSG_LEG_CASE(LM)                                                                                           \
   case LM:                                                                                                         \
-    e = launch_s_lmax<LM>(n_g, K_dev, L.n, F, nt, L.lmax, L.w, L.sf, p.dim, p.span, S, ld, ctx->opt.uplo, s); \
+    e = launch_s_lmax<LM>(n_g, K_dev, L.n, F, nt, L.lmax, L.w, L.h, L.sf, p.dim, p.span, S, p.tail ? H : nullptr, \
+                          ld, ctx->opt.uplo, s);                                                                 \
     break;
     HSG_LEG_CASE(0) HSG_LEG_CASE(1) HSG_LEG_CASE(2) HSG_LEG_CASE(3) HSG_LEG_CASE(4) HSG_LEG_CASE(5)
     HSG_LEG_CASE(6) HSG_LEG_CASE(7) HSG_LEG_CASE(8) HSG_LEG_CASE(9) HSG_LEG_CASE(10)
@@ -353,10 +407,10 @@ hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *K_dev, const
 }
 
 hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *K_dev, const double2 *F, const LegendrePlan &p,
-                        void *ws, double2 *S, long long ld, cudaStream_t s) {
+                        void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s) {
   hsgen_status st = legendre_upload(ctx, n_g, p, ws, s);
   if (st != HSGEN_OK) return st;
-  return legendre_launch(ctx, n_g, K_dev, F, p, ws, S, ld, s);
+  return legendre_launch(ctx, n_g, K_dev, F, p, ws, S, H, ld, s);
 }
 
 }  // namespace hsg

@@ -89,7 +89,7 @@ extern "C" hsgen_status hsgen_coefficients_noalloc(hsgen_ctx *ctx, int n_g, cons
   for (int t = 0; t < nt; ++t) {
     int n = (int)ctx->atoms_of_type[t].size();
     if (!n) continue;
-    HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, n_g, kvec, F + (size_t)t * n_g * kRadStride,
+    HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lc, n_g, kvec, F + (size_t)t * n_g * kRadStride,
                                         ctx->d_atoms_by_type + ctx->atoms_by_type_start[t], n, ctx->d_pos,
                                         ctx->d_rot, ctx->d_off, 0, ctx->types[t].dpad, (double2 *)W, ldw, s));
   }

@@ -1224,7 +1224,10 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
     return r;
   };
   const size_t o_kv = take(sizeof(double) * 3 * (size_t)std::max<long long>(sum_ng, 1));
-  const size_t o_F = take(sizeof(double2) * (size_t)nt * max_ng * kRadStride);
+  // radial factors: one scratch reused k-point by k-point, or (Legendre form,
+  // which reads them after the group's contraction) one region per k-point
+  const size_t o_F = take(sizeof(double2) * (size_t)nt * (leg ? (size_t)std::max<long long>(sum_ng, 1) : max_ng) *
+                          kRadStride);
   const size_t o_W = take(sizeof(double2) * (size_t)depth * max_ng);
   const size_t o_X = take(sizeof(double2) * (size_t)depth * max_ng);
   size_t max_group = 0;
@@ -1364,11 +1367,12 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           __nv_bfloat16 *Wsl = slice_base(k, (int)gi), *Xsl = Wsl + 3 * slices * plane,
                         *Ysl = Xsl + 3 * slices * plane;
           int *eW = d_exp + 3 * kv_off[k], *eX = eW + ng, *eY = eX + ng;
-          HSG_LAUNCH(ctx, launch_radial(ng, kd, nt, ctx->d_radial, F, s));
+          double2 *Fk = leg ? F + (size_t)nt * kv_off[k] * kRadStride : F;
+          HSG_LAUNCH(ctx, launch_radial(ng, kd, nt, ctx->d_radial, Fk, s));
           for (int t = 0; t < nt; ++t) {
             const int n = (int)ctx->atoms_of_type[t].size();
             if (!n) continue;
-            HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lmax, ng, kd, F + (size_t)t * ng * kRadStride,
+            HSG_LAUNCH(ctx, launch_coefficients(ctx->types[t].lc, ng, kd, Fk + (size_t)t * ng * kRadStride,
                                                 ctx->d_atoms_by_type + ctx->atoms_by_type_start[t], n, ctx->d_pos,
                                                 ctx->d_rot, ctx->d_off, 0, ctx->types[t].dpad, W, depth, s));
           }
@@ -1376,12 +1380,8 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           hsgen_status st2 = tapply_split(ctx, ng, 0, na, Wsl, ldk, eW, X, depth, slices, s);
           if (st2 != HSGEN_OK) return st2;
           HSG_LAUNCH(ctx, launch_slice(X, depth, depth, nullptr, slices, 3, Xsl, ldk, plane, eX, ng, s));
-          if (leg) {
-            hsgen_status st3 = legendre_launch(ctx, ng, kd, F, plans[k], ws + o_leg[k], (double2 *)S[k], ld[k], s);
-            if (st3 != HSGEN_OK) return st3;
-          } else {
+          if (!leg)
             HSG_LAUNCH(ctx, launch_slice(W, depth, depth, ctx->d_urow, slices, 2, Ysl, ldk, plane, eY, ng, s));
-          }
         }
         for (int sg = 0; sg < nseg; ++sg) {
           const size_t li = gi * nseg + sg;
@@ -1396,6 +1396,14 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           P.status = ctx->d_status;
           P.timeout_ns = (unsigned long long)ctx->opt.wait_timeout_ns;
           HSG_LAUNCH(ctx, launch_gemm(P, s));
+        }
+        // Legendre form: S, and H's spherical tail added after the contraction wrote H
+        for (int k = groups[gi].first; k < groups[gi].second && leg; ++k) {
+          if (n_g[k] <= 0) continue;
+          hsgen_status st3 = legendre_launch(ctx, n_g[k], d_kv + 3 * kv_off[k],
+                                             F + (size_t)nt * kv_off[k] * kRadStride, plans[k], ws + o_leg[k],
+                                             (double2 *)S[k], (double2 *)H[k], ld[k], s);
+          if (st3 != HSGEN_OK) return st3;
         }
       }
       return HSGEN_OK;

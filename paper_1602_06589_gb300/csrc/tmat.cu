@@ -75,7 +75,10 @@ __global__ void legendre_table_kernel(int n, const double *x, int lt, double *ta
 }
 
 struct TParams {
-  int lmax, nl, dpad, nq;
+  int lmax;     // species l_max: strides of the radial integrals I[l][l'][l'']
+  int nl;       // N_L of the T built here (the contraction's, (lc+1)^2)
+  int lns;      // l_nonsph: Gaunt part only for l, l' <= lns (Fig. Tmat_structure)
+  int dpad, nq;
   const double *I[4];  // uu, uud, udu, udud on the device
   const double *el, *un2;
 };
@@ -98,7 +101,7 @@ __global__ void tmatrix_kernel(TParams p, const double *__restrict__ xw, const d
   int n3 = 2 * p.lmax + 1;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   int lo = lp > l ? lp - l : l - lp;
-  for (int lpp = lo; lpp <= l + lp; lpp += 2) {
+  for (int lpp = lo; lpp <= l + lp && l <= p.lns && lp <= p.lns; lpp += 2) {
     if ((mpp < 0 ? -mpp : mpp) > lpp) continue;
     double q = 0.0;
     for (int g = 0; g < p.nq; ++g) q += w[g] * pbar(tab, g, lp, mp) * pbar(tab, g, l, m) * pbar(tab, g, lpp, mpp);
@@ -152,13 +155,14 @@ cudaError_t launch_tmatrix(const Species &sp, double2 *d_T, double *scratch, cud
   legendre_table_kernel<<<1, 64, 0, s>>>(nq, xw, 2 * sp.lmax, tab);
   TParams p;
   p.lmax = sp.lmax;
-  p.nl = sp.nl;
+  p.nl = sp.nlc;
+  p.lns = sp.lns;
   p.dpad = sp.dpad;
   p.nq = nq;
   for (int k = 0; k < 4; ++k) p.I[k] = dI + k * nI;
   p.el = del;
   p.un2 = dun2;
-  int nt = sp.nl * sp.nl;
+  int nt = sp.nlc * sp.nlc;
   tmatrix_kernel<<<(nt + 127) / 128, 128, 0, s>>>(p, xw, tab, d_T);
   return cudaGetLastError();
 }

@@ -39,7 +39,7 @@ class Options(C.Structure):
 class TypeDesc(C.Structure):
     _fields_ = [("lmax", C.c_int), ("rmt", C.c_double), ("u", _dp), ("du", _dp), ("udot", _dp), ("dudot", _dp),
                 ("wronskian", _dp), ("udot_norm2", _dp), ("e_l", _dp), ("I_uu", _dp), ("I_uud", _dp),
-                ("I_udu", _dp), ("I_udud", _dp), ("T_override", _dp)]
+                ("I_udu", _dp), ("I_udud", _dp), ("T_override", _dp), ("lmax_nonsph", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -135,6 +135,8 @@ class _TypeArrays:
             d = self.arr[i]
             d.lmax = int(t.lmax)
             d.rmt = float(t.rmt)
+            lns = getattr(t, "lmax_nonsph", None)
+            d.lmax_nonsph = -1 if lns is None else int(lns)
             for k in ("u", "du", "udot", "dudot", "udot_norm2", "e_l", "I_uu", "I_uud", "I_udu", "I_udud"):
                 a = np.ascontiguousarray(getattr(t, k), dtype=np.float64)
                 self.keep.append(a)
