@@ -423,6 +423,8 @@ def main():
     ap.add_argument("--n-g", type=int, default=0, help="override N_G (smaller cases for profiling)")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="also time one FP64-form step on the same workload")
+    ap.add_argument("--l-nonsph", type=int, default=-1,
+                    help="l_nonsph of every species (default: l_max, a dense T)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip hsgen_autotune before the warm-up (split form)")
     ap.add_argument("--s-form", choices=["contraction", "legendre"], default="contraction",
@@ -435,6 +437,9 @@ def main():
     from workloads import make_config
 
     w = make_config(args.config, n_g_override=args.n_g or None)
+    if args.l_nonsph >= 0:  # T's non-spherical part only for l, l' <= l_nonsph (Fig. Tmat_structure)
+        for ty in w.system.types:
+            ty.lmax_nonsph = min(args.l_nonsph, ty.lmax)
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -514,8 +519,17 @@ def main():
 
     # dominant kernel: the H/S contraction
     c_ms = statistics.mean(contract_ms)
-    # with S in the Legendre form the contraction computes H only (half of F_HS)
-    f_contract = fal["F_HS"] / 2 if st.get("s_form") == hsgen.S_LEGENDRE else fal["F_HS"]
+    # with S in the Legendre form the contraction computes H only (half of F_HS),
+    # over the rows l <= l_nonsph of each atom
+    if st.get("s_form") == hsgen.S_LEGENDRE:
+        nlc = []
+        for t in sysm.type_of_atom:
+            ty = sysm.types[t]
+            lc = ty.lmax if getattr(ty, "lmax_nonsph", None) is None else min(ty.lmax_nonsph, ty.lmax)
+            nlc.append((lc + 1) ** 2)
+        f_contract = fl.algorithmic_flops(n, nlc)["F_HS"] / 2
+    else:
+        f_contract = fal["F_HS"]
     if precision == hsgen.SPLIT:
         slices = st["slices"]
         lp_flops = f_contract * slices * (slices + 1) / 2  # bf16 products actually executed
@@ -542,6 +556,7 @@ def main():
         "config": {"workload": workload_name(args.config, w), "form": args.form,
                    "s_form": "legendre (Eq. overlap_no_m, FP64)" if st.get("s_form") == hsgen.S_LEGENDRE
                    else "contraction",
+                   "l_nonsph": args.l_nonsph if args.l_nonsph >= 0 else "l_max",
                    "slices": st["slices"] if precision == hsgen.SPLIT else None,
                    "schedule": ({"kseg_blocks": tuned["kseg_blocks"], "tile_band": tuned["tile_band"],
                                  "autotuned": not args.no_autotune} if precision == hsgen.SPLIT else None),
