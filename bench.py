@@ -105,7 +105,7 @@ def _traffic(config: int):
 
     here = os.path.dirname(os.path.abspath(__file__))
     try:
-        with open(os.path.join(here, "profiles", "split_gemm_dram_traffic_config4.json")) as f:
+        with open(os.path.join(here, "profiles", "split_gemm_dram_traffic_256atoms_NG20000.json")) as f:
             rec = json.load(f)
         with open(os.path.join(here, "paper_1602_06589_gb300", "csrc", "split.cu"), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
@@ -140,8 +140,11 @@ def oracle_sample_time(system, kvec, m: int):
 
 def workload_name(ci, w):
     s = w.system
-    return (f"{s.n_atoms} atoms / {len(s.types)} species, l_max {max(t.lmax for t in s.types)}, "
-            f"N_G {w.kvecs[0].shape[0]}, {len(w.kvecs)} k-point(s) (config {ci})")
+    ngs = [k.shape[0] for k in w.kvecs]
+    ng = f"{ngs[0]}" if len(set(ngs)) == 1 else f"{min(ngs)}-{max(ngs)}"
+    lm = sorted({t.lmax for t in s.types})
+    return (f"{s.n_atoms} atoms / {len(s.types)} species, l_max {'/'.join(map(str, lm))}, "
+            f"N_G {ng}, {len(w.kvecs)} k-point(s)")
 
 
 def run_reference(args, w):
