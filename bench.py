@@ -593,16 +593,25 @@ def main():
         if dist:
             dist.barrier()
         e_steps = max(1, min(args.steps, 3))
+        walls, dev_ms, up_ms, down_ms = [], [], [], []
         t0 = time.perf_counter()
         for _ in range(e_steps):
+            t1 = time.perf_counter()
             hsgen.hsgen_build_HS(g.ctx, n, kh.data_ptr(), Hh.data_ptr(), Sh.data_ptr(), n, stream.cuda_stream)
+            walls.append(time.perf_counter() - t1)
+            est = g.stats()
+            dev_ms.append(est["ms_total"])  # the build's device time, without the copies
+            up_ms.append(est["ms_upload"])
+            down_ms.append(est["ms_download"])
         te = (time.perf_counter() - t0) / e_steps
         if dist:
             t = torch.tensor([te], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
         line["e2e"] = {"value": te / world, "unit": "s/k-point", "h2d_bytes_per_step": int(kh.numel() * 8),
-                       "d2h_bytes_per_step": int(2 * n * n * 16)}
+                       "d2h_bytes_per_step": int(2 * n * n * 16),
+                       "calls_s": [round(x, 4) for x in walls], "device_ms": [round(x, 1) for x in dev_ms],
+                       "upload_ms": [round(x, 1) for x in up_ms], "download_ms": [round(x, 1) for x in down_ms]}
         del Hh, Sh
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

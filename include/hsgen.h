@@ -121,6 +121,10 @@ typedef struct {
   double ms_s;             /* S in the Legendre form (0 otherwise)              */
   int kseg_blocks;         /* split form: depth segment (64-deep blocks) in use */
   int tile_band;           /* split form: column blocks per tile band in use    */
+  double ms_upload;        /* host inputs/outputs: K_t upload and zeroing of    */
+                           /* the device staging of H, S, before the build      */
+  double ms_download;      /* host outputs: copy-out time after the build ends  */
+                           /* (the part not overlapped with the last tiles)     */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -141,17 +145,20 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
 
 /* Builds H and S for one k-point: kvec[n_g][3] are the Cartesian vectors
  * K_t = k + G_t (host or device pointer). H and S are complex128 column-major
- * n_g x n_g with leading dimension ld >= n_g: device pointers (written
- * asynchronously on `cuda_stream`, a cudaStream_t or NULL for the default
- * stream; only the triangle named by opt.uplo is written unless
- * opt.fill_full) or host pointers (computed in a library-owned device buffer
+ * n_g x n_g with leading dimension ld >= n_g: device pointers (written on
+ * `cuda_stream`, a cudaStream_t or NULL for the default stream; only the
+ * triangle named by opt.uplo is written unless opt.fill_full; the FP64 form
+ * returns without waiting, the split form waits for the stream so that it
+ * can read the status word of its bounded waits and report HSGEN_ETIMEOUT
+ * from this call) or host pointers (computed in a library-owned device buffer
  * and copied back in full, ld x n_g entries: the other triangle is zero
- * unless opt.fill_full; the call returns after the copy). Diagonal imaginary
- * parts are set to 0. */
+ * unless opt.fill_full; the call returns after the copy; in the split form
+ * the copies of finished column bands run on a library-owned stream while
+ * the last tiles are computed). Diagonal imaginary parts are set to 0. */
 hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);
 
-/* Builds H and S for n_k k-points in one go (D22: one H,S per k-point):
+/* Builds H and S for n_k k-points in one go (one H, S per k-point, Sec. 2.3):
  * n_g[k], kvec[k] (host pointers to [n_g[k]][3]), H[k], S[k] device
  * pointers with leading dimension ld[k]. All k-points' contraction tiles run
  * in one persistent launch over a grouped tile queue. */

@@ -45,6 +45,17 @@ static bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory (a copy into pageable memory would hold the host
+// thread until it ends, so band-by-band copies need pinned buffers).
+static bool is_pinned_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 static hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes) {
   if (w.bytes >= bytes) return HSGEN_OK;
   if (w.ptr) {
@@ -370,6 +381,7 @@ struct KpointJob {
   double2 *H, *S;
   long long ld;
   const LegendrePlan *leg = nullptr;  // S in the Legendre form (else the contraction)
+  CopyOut copy;                       // host outputs copied band by band during the last segment
 };
 
 // Device workspace layout for one k-point (byte offsets).
@@ -436,8 +448,9 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
     }
     if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
     if (split) {
+      const bool last = ci + 1 == chunks.size();
       hsgen_status st = split_chunk(ctx, n_g, a0, a1, W, X, L.ldw, job.H, job.leg ? nullptr : job.S, job.ld,
-                                    ci > 0, ws + L.split, slices, s, rec);
+                                    ci > 0, ws + L.split, slices, s, rec, last ? &job.copy : nullptr);
       if (st != HSGEN_OK) return st;
     } else {
       for (int t = 0; t < nt; ++t) {
@@ -561,6 +574,8 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   job.n_g = n_g;
   job.ld = ld;
   job.kvec_dev = kvec;
+  const bool host_io = !hdev || !kdev;
+  if (host_io) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[7], s));
   if (!kdev) {
     HSG_CUDA(ctx, cudaMemcpyAsync(ws + L.kvec, kvec, sizeof(double) * 3 * n_g, cudaMemcpyHostToDevice, s));
     job.kvec_dev = (const double *)(ws + L.kvec);
@@ -598,13 +613,31 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
                          "build_HS: l_nonsph < l_max with the Legendre form needs every K_t on one lattice k + G");
     }
   }
+  // host outputs of the split form: H (and S from the contraction) leave the
+  // device band by band while the last depth segment still runs, unless a
+  // later step (mirroring, H's spherical tail) still writes them
+  if (!hdev && split && !ctx->opt.fill_full && !(job.leg && job.leg->tail) && is_pinned_host(H) &&
+      (job.leg || is_pinned_host(S))) {
+    job.copy.H = H;
+    job.copy.S = job.leg ? nullptr : S;
+  }
   ctx->launches = 0;
   st = run_kpoint(ctx, job, s, ws, L, true);
-  if (st != HSGEN_OK) return st;
-  if (!hdev) {
-    HSG_CUDA(ctx, cudaMemcpyAsync(H, job.H, hs_bytes, cudaMemcpyDeviceToHost, s));
-    HSG_CUDA(ctx, cudaMemcpyAsync(S, job.S, hs_bytes, cudaMemcpyDeviceToHost, s));
+  if (st != HSGEN_OK) {
+    // no copy into the caller's buffers may still be running after an error
+    if (job.copy.H && ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    return st;
   }
+  if (!hdev) {
+    if (job.copy.H) {
+      st = split_join_copies(ctx, s);
+      if (st != HSGEN_OK) return st;
+    } else {
+      HSG_CUDA(ctx, cudaMemcpyAsync(H, job.H, hs_bytes, cudaMemcpyDeviceToHost, s));
+    }
+    if (!job.copy.S) HSG_CUDA(ctx, cudaMemcpyAsync(S, job.S, hs_bytes, cudaMemcpyDeviceToHost, s));
+  }
+  if (host_io) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[8], s));
   if (split) {
     st = split_check_status(ctx, s);
     if (st != HSGEN_OK) return st;
@@ -618,6 +651,7 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   ctx->phase_used[0] = atom_chunks(ctx).size() == 1;
   ctx->phase_used[1] = 1;
   ctx->phase_used[2] = job.leg != nullptr;
+  ctx->phase_used[3] = host_io;
   return HSGEN_OK;
 }
 
@@ -710,6 +744,7 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
   hsgen_stats st = ctx->stats;
   st.ms_coefficients = st.ms_tapply = st.ms_slice = st.ms_contract = st.ms_total = st.ms_s = 0.0;
+  st.ms_upload = st.ms_download = 0.0;
   if (ctx->phase_used[1]) {
     float ms = 0.f;
     HSG_CUDA(ctx, cudaEventSynchronize(ctx->ev[5]));
@@ -721,6 +756,10 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
       if (cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]) == cudaSuccess) st.ms_contract = ms;
     }
     if (ctx->phase_used[2] && cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[6]) == cudaSuccess) st.ms_s = ms;
+    if (ctx->phase_used[3]) {
+      if (cudaEventElapsedTime(&ms, ctx->ev[7], ctx->ev[0]) == cudaSuccess) st.ms_upload = ms;
+      if (cudaEventElapsedTime(&ms, ctx->ev[5], ctx->ev[8]) == cudaSuccess) st.ms_download = ms;
+    }
     cudaGetLastError();
   }
   st.workspace_bytes = (long long)(ctx->ws_main.bytes + ctx->ws_out.bytes + ctx->ws_leg.bytes);

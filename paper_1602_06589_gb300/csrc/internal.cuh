@@ -89,12 +89,15 @@ struct hsgen_ctx {
   int kseg_blocks = 128;            // split form: k-blocks (64 deep) per H/S launch
   int tile_band = 16;               // split form: column blocks per band of the tile order
   int tiles_band = 0;               // band the cached tile list was built with
+  std::vector<int2> tiles_host;     // host copy of that list (column bands of the overlapped copies)
+  cudaStream_t copy_stream = nullptr;  // host outputs: copies of finished column bands
+  cudaEvent_t copy_ev = nullptr;       // orders each copy after the launch that finished its bands
   hsg::Workspace ws_batch;          // batched k-points: per-k slices, tables, shared scratch
   cudaGraphExec_t batch_exec = nullptr;  // captured kernel sequence of the last batch
   cudaStream_t capture_stream = nullptr; // private stream the batch sequence is captured on
   std::vector<long long> batch_key;      // what that graph was captured for
   // timing
-  cudaEvent_t ev[8]{};
+  cudaEvent_t ev[10]{};
   bool events_ready = false;
   hsgen_stats stats{};
   long long launches = 0;           // kernels launched by the current call

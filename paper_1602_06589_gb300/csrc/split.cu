@@ -1074,7 +1074,7 @@ hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
 
 hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 *W, double2 *X, long long ldw,
                          double2 *H, double2 *S, long long ld, bool accumulate, void *ws, int slices,
-                         cudaStream_t s, bool record) {
+                         cudaStream_t s, bool record, const CopyOut *co) {
   if (ctx->split_slices != slices) {
     hsgen_status st = split_prepare_types(ctx, slices);
     if (st != HSGEN_OK) return st;
@@ -1108,6 +1108,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       ctx->tiles_n = -1;
       HSG_CUDA(ctx, cudaMalloc(&ctx->d_tiles, sizeof(int2) * std::max<size_t>(tl.size(), 1)));
       HSG_CUDA(ctx, cudaMemcpy(ctx->d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
+      ctx->tiles_host = tl;
       ctx->tiles_n = n_g;
       ctx->tiles_uplo = uplo;
       ctx->tiles_band = ctx->tile_band;
@@ -1131,9 +1132,62 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
     P.nprob = S ? 2 : 1;
     P.ntiles = P.nprob * per;
-    HSG_LAUNCH(ctx, launch_gemm(P, s));
+    const bool last = kb0 + seg >= nkb_all;
+    if (!last || !co || (!co->H && !(S && co->S))) {
+      HSG_LAUNCH(ctx, launch_gemm(P, s));
+      continue;
+    }
+    // last segment with host outputs: one problem at a time, in groups of
+    // whole column bands (at least a few waves of tiles each)
+    if (!ctx->copy_stream) HSG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    if (!ctx->copy_ev) HSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->copy_ev, cudaEventDisableTiming));
+    const long long min_tiles = 4 * max_pairs();
+    const int bandw = std::max(1, ctx->tiles_band);
+    const std::vector<int2> &tl = ctx->tiles_host;
+    if ((long long)tl.size() != per) return set_err(ctx, HSGEN_EINVAL, "split: tile list out of date");
+    for (int k = 0; k < P.nprob; ++k) {
+      GemmParams Q = P;
+      Q.prob[0] = P.prob[k];
+      Q.mapA[0] = P.mapA[k];
+      Q.mapB[0] = P.mapB[k];
+      Q.prob[0].tile_begin = 0;
+      Q.nprob = 1;
+      void *dst = (k == 0) ? co->H : co->S;
+      if (!dst) {
+        Q.ntiles = per;
+        HSG_LAUNCH(ctx, launch_gemm(Q, s));
+        continue;
+      }
+      for (long long t0 = 0; t0 < per;) {
+        long long t1 = t0;
+        while (t1 < per) {
+          const int band = tl[t1].y / bandw;
+          while (t1 < per && tl[t1].y / bandw == band) ++t1;
+          if (t1 - t0 >= min_tiles) break;
+        }
+        Q.prob[0].tile_list = (const int2 *)ctx->d_tiles + t0;
+        Q.ntiles = t1 - t0;
+        HSG_LAUNCH(ctx, launch_gemm(Q, s));
+        // the group holds every tile of columns [c0, c1)
+        const long long c0 = (long long)(tl[t0].y / bandw) * bandw * BN;
+        const long long c1 = std::min<long long>(n_g, (long long)(tl[t1 - 1].y / bandw + 1) * bandw * BN);
+        const double2 *src = Q.prob[0].C;
+        HSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, s));
+        HSG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev, 0));
+        HSG_CUDA(ctx, cudaMemcpyAsync((double2 *)dst + c0 * ld, src + c0 * ld, sizeof(double2) * (c1 - c0) * ld,
+                                      cudaMemcpyDeviceToHost, ctx->copy_stream));
+        t0 = t1;
+      }
+    }
     }
   }
+  return HSGEN_OK;
+}
+
+hsgen_status split_join_copies(hsgen_ctx *ctx, cudaStream_t s) {
+  if (!ctx->copy_stream) return HSGEN_OK;
+  HSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, ctx->copy_stream));
+  HSG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->copy_ev, 0));
   return HSGEN_OK;
 }
 
@@ -1150,7 +1204,7 @@ hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s) {
   return HSGEN_OK;
 }
 
-// Many k-points (D22): per k-point the cheap steps (radial factors,
+// Many k-points (one H, S per k-point, Sec. 2.3): per k-point the cheap steps (radial factors,
 // coefficients, slicing, X = T W) fill that k-point's slice buffers; then one
 // persistent grouped launch per depth segment runs the H and S tiles of every
 // k-point of a group (uneven N_G and mixed l_max share one tile queue). The
@@ -1433,6 +1487,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   ctx->phase_used[0] = 0;
   ctx->phase_used[1] = 0;
   ctx->phase_used[2] = 0;
+  ctx->phase_used[3] = 0;
   ctx->stats.s_form = leg ? HSGEN_S_LEGENDRE : HSGEN_S_CONTRACTION;
   return split_check_status(ctx, s);
 }
@@ -1452,6 +1507,10 @@ void split_release(hsgen_ctx *ctx) {
   ctx->batch_key.clear();
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   ctx->capture_stream = nullptr;
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  ctx->copy_stream = nullptr;
+  if (ctx->copy_ev) cudaEventDestroy(ctx->copy_ev);
+  ctx->copy_ev = nullptr;
   if (ctx->ws_batch.ptr) cudaFree(ctx->ws_batch.ptr);
   ctx->ws_batch.ptr = nullptr;
   ctx->ws_batch.bytes = 0;

@@ -22,11 +22,20 @@ int choose_slices(double target_rel_err, int override_slices);
 size_t split_workspace_bytes(int n_g, int chunk_depth, int slices);
 // Slices the T matrices once per species (called by hsgen_set_atoms in split mode).
 hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices);
+// Host outputs of the last pass: the last depth segment runs as launches over
+// groups of whole column bands, and after each launch the copy stream moves
+// the finished columns of that matrix (all ld rows of each) to the host
+// buffer, so the copies overlap the remaining tiles. Null: not copied here.
+struct CopyOut {
+  void *H = nullptr, *S = nullptr;
+};
 // One pass (one chunk of atoms [a0, a1)) of the split path: slice W, X = T W,
 // slice X and U W, then one triangle of H (+)= W^H X and S (+)= (U W)^H W.
 hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 *W, double2 *X, long long ldw,
                          double2 *H, double2 *S, long long ld, bool accumulate, void *ws, int slices,
-                         cudaStream_t s, bool record);
+                         cudaStream_t s, bool record, const CopyOut *co = nullptr);
+// Makes `s` wait for the copies split_chunk queued on the copy stream.
+hsgen_status split_join_copies(hsgen_ctx *ctx, cudaStream_t s);
 // Reads the device status word of the split launches of this call (bounded waits).
 hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s);
 // Batched k-points in one persistent launch; HSGEN_ENOTSUP when not applicable

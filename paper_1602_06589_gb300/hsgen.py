@@ -47,7 +47,8 @@ class Stats(C.Structure):
                 ("ms_contract", C.c_double), ("ms_total", C.c_double), ("flops_algorithmic", C.c_double),
                 ("precision", C.c_int), ("slices", C.c_int), ("n_kpoints", C.c_int),
                 ("workspace_bytes", C.c_longlong), ("kernel_launches", C.c_longlong), ("s_form", C.c_int),
-                ("ms_s", C.c_double), ("kseg_blocks", C.c_int), ("tile_band", C.c_int)]
+                ("ms_s", C.c_double), ("kseg_blocks", C.c_int), ("tile_band", C.c_int),
+                ("ms_upload", C.c_double), ("ms_download", C.c_double)]
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",

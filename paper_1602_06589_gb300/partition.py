@@ -1,6 +1,6 @@
 """Work partition across ranks (one process per GPU).
 
-k-points are independent (one H, S per k-point, Sec. 2.2), so a batch of
+k-points are independent (one H, S per k-point, Sec. 2.3), so a batch of
 k-points is dealt round-robin to ranks with no data exchange. Within one
 k-point the triangle of H and S can be dealt as square tiles in a 2-D
 block-cyclic layout over a prow x pcol process grid (the layout a distributed

@@ -1,4 +1,4 @@
-"""Many k-points in one call (D22: one H, S per k-point), through
+"""Many k-points in one call (one H, S per k-point, Sec. 2.3), through
 hsgen_build_HS_batched: uneven N_G and mixed l_max in one grouped launch,
 captured as a CUDA graph. The batched result must equal the k-point-by-k-point
 result bit for bit (same slices, same tile schedule), match the oracle on

@@ -1,6 +1,6 @@
 """GPU parity of the FP64 form against the oracle, through the C ABI.
 
-Tolerances (BASELINE north-star): relative Frobenius error <= 1e-12 over the
+Tolerances (FP64 form): relative Frobenius error <= 1e-12 over the
 written triangle, and per entry |dH_ij| <= 1e-10 ||w_i|| ||x_j|| (the
 Cauchy-Schwarz scale of a dot product; S uses ||y_j||).
 """
