@@ -472,7 +472,8 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
   if (job.leg) {
-    hsgen_status st = legendre_S(ctx, n_g, job.kvec_dev, F, *job.leg, ctx->ws_leg.ptr, job.S, job.H, job.ld, s);
+    hsgen_status st = legendre_S(ctx, n_g, job.kvec_dev, F, *job.leg, ctx->ws_leg.ptr, job.S, job.H, job.ld, s,
+                                 job.copy.S);
     if (st != HSGEN_OK) return st;
     if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
   }
@@ -613,13 +614,15 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
                          "build_HS: l_nonsph < l_max with the Legendre form needs every K_t on one lattice k + G");
     }
   }
-  // host outputs of the split form: H (and S from the contraction) leave the
-  // device band by band while the last depth segment still runs, unless a
-  // later step (mirroring, H's spherical tail) still writes them
+  // pinned host outputs of the split form: H and S leave the device group by
+  // group of finished columns while later groups compute, unless a later
+  // step (mirroring, H's spherical tail) still writes them; S in the Legendre
+  // form is copied that way for the upper triangle (its tiles run column by
+  // column there)
   if (!hdev && split && !ctx->opt.fill_full && !(job.leg && job.leg->tail) && is_pinned_host(H) &&
-      (job.leg || is_pinned_host(S))) {
+      is_pinned_host(S)) {
     job.copy.H = H;
-    job.copy.S = job.leg ? nullptr : S;
+    job.copy.S = (job.leg && ctx->opt.uplo != 'U') ? nullptr : S;
   }
   ctx->launches = 0;
   st = run_kpoint(ctx, job, s, ws, L, true);

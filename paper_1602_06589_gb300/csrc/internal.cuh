@@ -147,13 +147,17 @@ size_t legendre_ws_bytes(const hsgen_ctx *ctx, int n_g, const LegendrePlan &p);
 // this k-point (F[type][t][l], as launch_radial writes them) and, when the plan
 // has a tail, adds H's spherical rows beyond each species' contraction into H;
 // ws holds legendre_ws_bytes. Asynchronous on s (host tables are staged by the copies).
+// S_host (pinned host, same ld; upper triangle only): S's finished column
+// groups are copied there on ctx->copy_stream while later groups compute.
 // The two halves of legendre_S, for graph capture: the host-table uploads and
-// kernel attributes (before a capture), then the kernel launches (capturable).
+// kernel attributes (before a capture), then the kernel launches (capturable
+// when S_host is null).
 hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, void *ws, cudaStream_t s);
 hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const double2 *F,
-                             const LegendrePlan &p, void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s);
+                             const LegendrePlan &p, void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s,
+                             void *S_host = nullptr);
 hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const double2 *F, const LegendrePlan &p,
-                        void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s);
+                        void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s, void *S_host = nullptr);
 // a2: T matrix of one species (device, dpad x dpad complex, column-major).
 cudaError_t launch_tmatrix(const Species &sp, double2 *d_T, double *scratch, cudaStream_t s);
 // Recurrence tables in constant memory (called once per device).

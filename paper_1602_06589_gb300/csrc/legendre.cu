@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
     int n_g, const double *__restrict__ K, const int *__restrict__ nco, const double2 *__restrict__ F, int n_types,
     const int *__restrict__ lmax_of, const double2 *__restrict__ wts, const double2 *__restrict__ htab,
     const double2 *__restrict__ SF, int d2, int d3, int s1, int s2, int s3, double2 *__restrict__ S,
-    double2 *__restrict__ H, long long ld, int uplo) {
+    double2 *__restrict__ H, long long ld, int uplo, long long x0) {
   constexpr int NLP = LMAX + 1;
   extern __shared__ double2 smem[];
   const int nlf = n_types * NLP;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
   __shared__ double rK[TILE][3], cK[TILE][3];
   __shared__ int rN[TILE][3], cN[TILE][3];
 
-  const long long x = blockIdx.x;
+  const long long x = x0 + blockIdx.x;  // tiles in order of hi (the column block for 'U')
   int hi = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
   while ((long long)hi * (hi + 1) / 2 > x) --hi;
   while ((long long)(hi + 1) * (hi + 2) / 2 <= x) ++hi;
@@ -206,18 +206,18 @@ __global__ void __launch_bounds__(LTHREADS) legendre_s_kernel(
 template <int L>
 cudaError_t launch_s_lmax(int n_g, const double *K, const int *nco, const double2 *F, int n_types, const int *lmax_of,
                           const double2 *wts, const double2 *htab, const double2 *SF, const int d[3], const int sp[3],
-                          double2 *S, double2 *H, long long ld, int uplo, cudaStream_t s) {
-  const long long nb = (n_g + TILE - 1) / TILE;
-  const long long ntiles = nb * (nb + 1) / 2;
+                          double2 *S, double2 *H, long long ld, int uplo, long long x0, long long ntiles,
+                          cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (H) {
     const size_t sm = sizeof(double2) * 3 * TILE * n_types * (L + 1);
     legendre_s_kernel<L, true><<<(unsigned)ntiles, LTHREADS, sm, s>>>(
-        n_g, K, nco, F, n_types, lmax_of, wts, htab, SF, d[1], d[2], sp[0], sp[1], sp[2], S, H, ld, uplo);
+        n_g, K, nco, F, n_types, lmax_of, wts, htab, SF, d[1], d[2], sp[0], sp[1], sp[2], S, H, ld, uplo, x0);
   } else {
     const size_t sm = sizeof(double2) * 2 * TILE * n_types * (L + 1);
     legendre_s_kernel<L, false><<<(unsigned)ntiles, LTHREADS, sm, s>>>(
-        n_g, K, nco, F, n_types, lmax_of, wts, htab, SF, d[1], d[2], sp[0], sp[1], sp[2], S, H, ld, uplo);
+        n_g, K, nco, F, n_types, lmax_of, wts, htab, SF, d[1], d[2], sp[0], sp[1], sp[2], S, H, ld, uplo, x0);
   }
   return cudaGetLastError();
 }
@@ -379,7 +379,7 @@ hsgen_status legendre_upload(hsgen_ctx *ctx, int n_g, const LegendrePlan &p, voi
 }
 
 hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *K_dev, const double2 *F, const LegendrePlan &p,
-                             void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s) {
+                             void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s, void *S_host) {
   const int nt = (int)ctx->types.size();
   const LegWs L = leg_ws(ctx, n_g, p, ws);
   {
@@ -389,28 +389,54 @@ hsgen_status legendre_launch(hsgen_ctx *ctx, int n_g, const double *K_dev, const
     HSG_CUDA(ctx, cudaGetLastError());
     ++ctx->launches;
   }
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (p.lmax) {
-#define HSG_LEG_CASE(LM)                                                                                           \
-  case LM:                                                                                                         \
-    e = launch_s_lmax<LM>(n_g, K_dev, L.n, F, nt, L.lmax, L.w, L.h, L.sf, p.dim, p.span, S, p.tail ? H : nullptr, \
-                          ld, ctx->opt.uplo, s);                                                                 \
+  const long long nb = (n_g + TILE - 1) / TILE;
+  const long long ntiles = nb * (nb + 1) / 2;
+  auto launch = [&](long long x0, long long cnt) -> hsgen_status {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (p.lmax) {
+#define HSG_LEG_CASE(LM)                                                                                         \
+  case LM:                                                                                                       \
+    e = launch_s_lmax<LM>(n_g, K_dev, L.n, F, nt, L.lmax, L.w, L.h, L.sf, p.dim, p.span, S,                    \
+                          p.tail ? H : nullptr, ld, ctx->opt.uplo, x0, cnt, s);                                \
     break;
-    HSG_LEG_CASE(0) HSG_LEG_CASE(1) HSG_LEG_CASE(2) HSG_LEG_CASE(3) HSG_LEG_CASE(4) HSG_LEG_CASE(5)
-    HSG_LEG_CASE(6) HSG_LEG_CASE(7) HSG_LEG_CASE(8) HSG_LEG_CASE(9) HSG_LEG_CASE(10)
+      HSG_LEG_CASE(0) HSG_LEG_CASE(1) HSG_LEG_CASE(2) HSG_LEG_CASE(3) HSG_LEG_CASE(4) HSG_LEG_CASE(5)
+      HSG_LEG_CASE(6) HSG_LEG_CASE(7) HSG_LEG_CASE(8) HSG_LEG_CASE(9) HSG_LEG_CASE(10)
 #undef HSG_LEG_CASE
-    default: break;
+      default: break;
+    }
+    HSG_CUDA(ctx, e);
+    ++ctx->launches;
+    return HSGEN_OK;
+  };
+  if (!S_host || ctx->opt.uplo != 'U') return launch(0, ntiles);
+  // Host output of S (upper triangle): the tiles of column block j are
+  // x in [j(j+1)/2, (j+1)(j+2)/2), so launches over whole column blocks,
+  // about 1/16 of the tiles each, leave finished columns that the copy
+  // stream moves to the host while the next launches compute.
+  if (!ctx->copy_stream) HSG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  if (!ctx->copy_ev) HSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->copy_ev, cudaEventDisableTiming));
+  const long long want = std::max<long long>(1, (ntiles + 15) / 16);
+  for (long long j0 = 0; j0 < nb;) {
+    long long j1 = j0 + 1;
+    while (j1 < nb && j1 * (j1 + 1) / 2 - j0 * (j0 + 1) / 2 < want) ++j1;
+    const long long x0 = j0 * (j0 + 1) / 2, x1 = j1 * (j1 + 1) / 2;
+    hsgen_status st = launch(x0, x1 - x0);
+    if (st != HSGEN_OK) return st;
+    const long long c0 = j0 * TILE, c1 = std::min<long long>(n_g, j1 * TILE);
+    HSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, s));
+    HSG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev, 0));
+    HSG_CUDA(ctx, cudaMemcpyAsync((double2 *)S_host + c0 * ld, S + c0 * ld, sizeof(double2) * (c1 - c0) * ld,
+                                  cudaMemcpyDeviceToHost, ctx->copy_stream));
+    j0 = j1;
   }
-  HSG_CUDA(ctx, e);
-  ++ctx->launches;
   return HSGEN_OK;
 }
 
 hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *K_dev, const double2 *F, const LegendrePlan &p,
-                        void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s) {
+                        void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s, void *S_host) {
   hsgen_status st = legendre_upload(ctx, n_g, p, ws, s);
   if (st != HSGEN_OK) return st;
-  return legendre_launch(ctx, n_g, K_dev, F, p, ws, S, H, ld, s);
+  return legendre_launch(ctx, n_g, K_dev, F, p, ws, S, H, ld, s, S_host);
 }
 
 }  // namespace hsg

@@ -1114,71 +1114,70 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       ctx->tiles_band = ctx->tile_band;
       ctx->tiles_count = (long long)tl.size();
     }
-    // The depth is cut into segments run as separate launches that add into
-    // H and S: shorter tiles keep the CTAs of one wave close together in k,
-    // so the A and B blocks they share stay in L2.
     const int nkb_all = (int)(w.ldk / BK);
     const int seg_kb = std::max(1, ctx->kseg_blocks);
-    for (int kb0 = 0; kb0 < nkb_all; kb0 += seg_kb) {
-    const int seg = std::min(seg_kb, nkb_all - kb0);
-    GemmParams P;
-    std::memset(&P, 0, sizeof(P));
-    P.s = slices;
-    P.status = ctx->d_status;
-    P.timeout_ns = tmo;
     const long long per = ctx->tiles_count;
-    if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, w.ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
-                     w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles, per, 0, slices))
-      return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
-    P.nprob = S ? 2 : 1;
-    P.ntiles = P.nprob * per;
-    const bool last = kb0 + seg >= nkb_all;
-    if (!last || !co || (!co->H && !(S && co->S))) {
+    // one launch: the tiles [t0, t0 + cnt) of the list, of H (and S), over
+    // the depth segment [kb0, kb0 + seg)
+    auto launch_seg = [&](long long t0, long long cnt, int kb0) -> hsgen_status {
+      const int seg = std::min(seg_kb, nkb_all - kb0);
+      GemmParams P;
+      std::memset(&P, 0, sizeof(P));
+      P.s = slices;
+      P.status = ctx->d_status;
+      P.timeout_ns = tmo;
+      if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, w.ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
+                       w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, slices))
+        return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
+      P.nprob = S ? 2 : 1;
+      P.ntiles = P.nprob * cnt;
       HSG_LAUNCH(ctx, launch_gemm(P, s));
-      continue;
+      return HSGEN_OK;
+    };
+    if (!co || (!co->H && !(S && co->S))) {
+      // The depth is cut into segments run as separate launches that add into
+      // H and S: shorter tiles keep the CTAs of one wave close together in k,
+      // so the A and B blocks they share stay in L2.
+      for (int kb0 = 0; kb0 < nkb_all; kb0 += seg_kb) {
+        hsgen_status st = launch_seg(0, per, kb0);
+        if (st != HSGEN_OK) return st;
+      }
+      return HSGEN_OK;
     }
-    // last segment with host outputs: one problem at a time, in groups of
-    // whole column bands (at least a few waves of tiles each)
+    // Host outputs: the same launches in column-band-group-major order (all
+    // depth segments of one group of whole bands, at least a few waves of
+    // tiles, then the next), so a group's finished columns go to the host on
+    // the copy stream while the later groups compute.
     if (!ctx->copy_stream) HSG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
     if (!ctx->copy_ev) HSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->copy_ev, cudaEventDisableTiming));
     const long long min_tiles = 4 * max_pairs();
     const int bandw = std::max(1, ctx->tiles_band);
     const std::vector<int2> &tl = ctx->tiles_host;
     if ((long long)tl.size() != per) return set_err(ctx, HSGEN_EINVAL, "split: tile list out of date");
-    for (int k = 0; k < P.nprob; ++k) {
-      GemmParams Q = P;
-      Q.prob[0] = P.prob[k];
-      Q.mapA[0] = P.mapA[k];
-      Q.mapB[0] = P.mapB[k];
-      Q.prob[0].tile_begin = 0;
-      Q.nprob = 1;
-      void *dst = (k == 0) ? co->H : co->S;
-      if (!dst) {
-        Q.ntiles = per;
-        HSG_LAUNCH(ctx, launch_gemm(Q, s));
-        continue;
+    for (long long t0 = 0; t0 < per;) {
+      long long t1 = t0;
+      while (t1 < per) {
+        const int band = tl[t1].y / bandw;
+        while (t1 < per && tl[t1].y / bandw == band) ++t1;
+        if (t1 - t0 >= min_tiles) break;
       }
-      for (long long t0 = 0; t0 < per;) {
-        long long t1 = t0;
-        while (t1 < per) {
-          const int band = tl[t1].y / bandw;
-          while (t1 < per && tl[t1].y / bandw == band) ++t1;
-          if (t1 - t0 >= min_tiles) break;
-        }
-        Q.prob[0].tile_list = (const int2 *)ctx->d_tiles + t0;
-        Q.ntiles = t1 - t0;
-        HSG_LAUNCH(ctx, launch_gemm(Q, s));
-        // the group holds every tile of columns [c0, c1)
-        const long long c0 = (long long)(tl[t0].y / bandw) * bandw * BN;
-        const long long c1 = std::min<long long>(n_g, (long long)(tl[t1 - 1].y / bandw + 1) * bandw * BN);
-        const double2 *src = Q.prob[0].C;
-        HSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, s));
-        HSG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev, 0));
-        HSG_CUDA(ctx, cudaMemcpyAsync((double2 *)dst + c0 * ld, src + c0 * ld, sizeof(double2) * (c1 - c0) * ld,
-                                      cudaMemcpyDeviceToHost, ctx->copy_stream));
-        t0 = t1;
+      for (int kb0 = 0; kb0 < nkb_all; kb0 += seg_kb) {
+        hsgen_status st = launch_seg(t0, t1 - t0, kb0);
+        if (st != HSGEN_OK) return st;
       }
-    }
+      // the group holds every tile of columns [c0, c1)
+      const long long c0 = (long long)(tl[t0].y / bandw) * bandw * BN;
+      const long long c1 = std::min<long long>(n_g, (long long)(tl[t1 - 1].y / bandw + 1) * bandw * BN);
+      HSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, s));
+      HSG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev, 0));
+      for (int k = 0; k < 2; ++k) {
+        void *dst = (k == 0) ? co->H : (S ? co->S : nullptr);
+        const double2 *src = (k == 0) ? H : S;
+        if (dst)
+          HSG_CUDA(ctx, cudaMemcpyAsync((double2 *)dst + c0 * ld, src + c0 * ld, sizeof(double2) * (c1 - c0) * ld,
+                                        cudaMemcpyDeviceToHost, ctx->copy_stream));
+      }
+      t0 = t1;
     }
   }
   return HSGEN_OK;

@@ -22,10 +22,11 @@ int choose_slices(double target_rel_err, int override_slices);
 size_t split_workspace_bytes(int n_g, int chunk_depth, int slices);
 // Slices the T matrices once per species (called by hsgen_set_atoms in split mode).
 hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices);
-// Host outputs of the last pass: the last depth segment runs as launches over
-// groups of whole column bands, and after each launch the copy stream moves
-// the finished columns of that matrix (all ld rows of each) to the host
-// buffer, so the copies overlap the remaining tiles. Null: not copied here.
+// Host outputs of the last pass: the H/S launches run group by group (groups
+// of whole column bands, every depth segment of a group before the next
+// group), and after each group the copy stream moves its finished columns
+// (all ld rows of each) to the host buffers, so the copies overlap the
+// remaining groups. Null: not copied here.
 struct CopyOut {
   void *H = nullptr, *S = nullptr;
 };

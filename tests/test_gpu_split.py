@@ -111,12 +111,15 @@ def test_split_host_pointers(hs):
 
 
 @pytest.mark.parametrize("uplo,s_form,chunk", [("U", "S_CONTRACTION", 0), ("L", "S_CONTRACTION", 0),
-                                              ("U", "S_LEGENDRE", 0), ("U", "S_CONTRACTION", 40)])
+                                              ("U", "S_LEGENDRE", 0), ("L", "S_LEGENDRE", 0),
+                                              ("U", "S_CONTRACTION", 40)])
 def test_pinned_host_outputs_match_device(hs, uplo, s_form, chunk):
-    """Pinned host outputs: the finished column bands of H (and of S from the
-    contraction) are copied to the host while the last depth segment runs
-    (several band groups at N_G 6000). The host result equals the build into
-    device buffers bit for bit, and the other triangle is overwritten with zeros."""
+    """Pinned host outputs: the H/S launches run group by group of column
+    bands and each group's finished columns are copied to the host while later
+    groups compute (several groups at N_G 6000; S in the Legendre form in
+    column groups of its own kernel for the upper triangle). The host result
+    equals the build into device buffers bit for bit, and the other triangle
+    is overwritten with zeros."""
     import torch
 
     w = make_config(2, n_g_override=6000)
