@@ -19,3 +19,4 @@ from .hsref import (  # noqa: F401
     HS_brute,
     threads,
 )
+from .reduce import hermitian_from_triangle, reduce_generalized  # noqa: F401
