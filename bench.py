@@ -268,6 +268,56 @@ def _cublas(torch):
     return lib
 
 
+def reduce_bench(args, w):
+    """The generalized-eigenproblem hand-off (Sec. 2.3, Eq. matrix_kohnsham) on
+    this workload: H, S from the split build plus a stand-in for the
+    interstitial part (S + I, H + diag(|K_t|^2)), then hsgen_reduce_generalized
+    (FP64 Cholesky of S and H~ = U^-H H U^-1 in place) timed with CUDA events;
+    each timed call starts from a fresh device copy of H, S (copy untimed)."""
+    import numpy as np
+    import torch
+
+    from paper_1602_06589_gb300 import hsgen
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    sysm, kv = w.system, w.kvecs[0]
+    n = kv.shape[0]
+    with hsgen.Generator(sysm, precision=hsgen.SPLIT) as g:
+        H, S = g.build(torch.from_numpy(kv).to(dev))
+        H += torch.diag(torch.from_numpy(np.sum(kv * kv, axis=1)).to(H)).triu()
+        S += torch.eye(n, dtype=S.dtype, device=dev)
+        build_s = g.stats()["ms_total"] * 1e-3
+        H0, S0 = H.clone(), S.clone()
+        times = []
+        for i in range(max(1, args.warmup) + args.steps):
+            H.copy_(H0)
+            S.copy_(S0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g.reduce(H, S, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= max(1, args.warmup):
+                times.append(e0.elapsed_time(e1) * 1e-3)
+    t = statistics.median(times)
+    flops = (8.0 / 3.0 + 8.0) * float(n) ** 3  # ZPOTRF n^3/3 + two ZTRSM n^3/2 complex MACs each, 8 flops per MAC
+    peaks = _peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0
+    achieved = flops / t / 1e12
+    line = {"metric": "generalized-eigenproblem reduction (FP64 Cholesky of S, H~ = U^-H H U^-1), s/k-point",
+            "impl": "reduce", "value": t, "unit": "s/k-point", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(1, args.warmup), "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.config, w), "interstitial": "stand-in S + I, H + diag(|K|^2)"},
+            "build_s_per_kpoint": build_s,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "cuSOLVER ZPOTRF + 2 cuBLAS ZTRSM (FP64)",
+                         "peak_source": "measured bf16 sustained x nominal fp64/bf16 ratio"}}
+    print(json.dumps(line), flush=True)
+
+
 def library_bars(args, w):
     """Library bars on the same workload, beside this library's split form:
     (1) cuBLAS ZGEMM (H = W^H X, full) + ZHERK (S = V^H V, V = diag(sqrt(u)) W,
@@ -435,6 +485,9 @@ def main():
     ap.add_argument("--library-bars", action="store_true",
                     help="time cuBLAS ZGEMM + ZHERK (FP64 and FP64-emulated) beside the split form, then exit")
     ap.add_argument("--bar-reps", type=int, default=1)
+    ap.add_argument("--reduce", action="store_true",
+                    help="time the generalized-eigenproblem hand-off (hsgen_reduce_generalized) on this "
+                         "workload, then exit")
     args = ap.parse_args()
 
     from workloads import make_config
@@ -448,6 +501,12 @@ def main():
         return
     if args.library_bars:
         library_bars(args, w)
+        return
+    if args.reduce:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        reduce_bench(args, w)
         return
 
     import numpy as np

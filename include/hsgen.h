@@ -54,7 +54,8 @@ typedef enum {
   HSGEN_ECUDA = 3,    /* CUDA runtime/driver error, or no usable sm_103a device */
   HSGEN_ETIMEOUT = 4, /* a bounded device wait gave up; results are invalid    */
   HSGEN_ENOTSUP = 5,  /* option combination not supported                      */
-  HSGEN_ENUMERIC = 6  /* |W_l| too small, NaN/Inf input, non-Hermitian T       */
+  HSGEN_ENUMERIC = 6  /* |W_l| too small, NaN/Inf input, non-Hermitian T,     */
+                      /* S not positive definite (hsgen_reduce_generalized)    */
 } hsgen_status;
 
 enum { HSGEN_FP64 = 0, HSGEN_SPLIT = 1 };
@@ -207,6 +208,22 @@ hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
  * FP64 form has nothing to tune: it builds once and returns HSGEN_OK. */
 hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);
+
+/* Hand-off to the generalized eigensolver (Sec. 2.3, Eq. matrix_kohnsham:
+ * H c = eps S c; no counterpart in the paper's H/S generation itself). H, S:
+ * device pointers, complex128 column-major n x n with leading dimension
+ * ld >= n (ld < 2^31), Hermitian with their opt.uplo triangle given (as
+ * hsgen_build_HS writes them; the other triangle is not read); S must be
+ * positive definite (the full problem's S: the muffin-tin part this library
+ * builds plus the interstitial part the caller adds). In place and in FP64:
+ * S's opt.uplo triangle becomes the Cholesky factor (U with S = U^H U for
+ * 'U', L with S = L L^H for 'L'; the other triangle is left as it was) and H
+ * becomes H~ = U^-H H U^-1 (= L^-1 H L^-H), written in full and exactly
+ * Hermitian, so that H~ y = eps y and c = U^-1 y (= L^-H y). Runs on
+ * `cuda_stream` and returns when it is done. HSGEN_ENUMERIC when S is not
+ * positive definite (H and S are then overwritten with partial results);
+ * HSGEN_EINVAL for host pointers, aliasing or bad sizes. */
+hsgen_status hsgen_reduce_generalized(hsgen_ctx *ctx, int n, void *H, void *S, long long ld, void *cuda_stream);
 
 hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *stats);
 const char *hsgen_last_error(const hsgen_ctx *ctx);

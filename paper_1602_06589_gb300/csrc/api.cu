@@ -36,7 +36,7 @@ static bool finite_all(const double *p, size_t n) {
   return true;
 }
 
-static bool is_device_ptr(const void *p) {
+bool is_device_ptr(const void *p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -56,7 +56,7 @@ static bool is_pinned_host(const void *p) {
   return a.type == cudaMemoryTypeHost;
 }
 
-static hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes) {
+hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes) {
   if (w.bytes >= bytes) return HSGEN_OK;
   if (w.ptr) {
     cudaError_t e = cudaFree(w.ptr);
@@ -785,6 +785,7 @@ void hsgen_destroy(hsgen_ctx *ctx) {
   if (ctx->ws_main.ptr) cudaFree(ctx->ws_main.ptr);
   if (ctx->ws_out.ptr) cudaFree(ctx->ws_out.ptr);
   if (ctx->ws_leg.ptr) cudaFree(ctx->ws_leg.ptr);
+  reduce_release(ctx);
   if (ctx->events_ready)
     for (auto &e : ctx->ev) cudaEventDestroy(e);
   delete ctx;

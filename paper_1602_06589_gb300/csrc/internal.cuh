@@ -80,6 +80,10 @@ struct hsgen_ctx {
   hsg::Workspace ws_main;           // W, X, radial factors, kvec copy, split slices
   hsg::Workspace ws_out;            // device H/S staging when the caller passes host pointers
   hsg::Workspace ws_leg;            // S in the Legendre form: coordinates, structure factors, tables
+  hsg::Workspace ws_red;            // generalized-eigenproblem reduction: factorization workspace, status
+  void *blas = nullptr;             // cublasHandle_t of the reduction
+  void *solver = nullptr;           // cusolverDnHandle_t of the reduction
+  int *h_info = nullptr;            // pinned host copy of the factorization status
   int split_slices = 0;             // slices the species' T were cut into
   int *d_status = nullptr;          // device status word of the split kernels
   int *h_status = nullptr;          // pinned host copy
@@ -107,6 +111,12 @@ struct hsgen_ctx {
 namespace hsg {
 
 // ---- error helpers ---------------------------------------------------------
+// True for device (or managed) memory.
+bool is_device_ptr(const void *p);
+// Grows a library workspace to at least `bytes` (contents not kept).
+hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes);
+// Frees the reduction's handles and buffers.
+void reduce_release(hsgen_ctx *ctx);
 hsgen_status set_err(hsgen_ctx *ctx, hsgen_status st, const std::string &msg);
 hsgen_status cuda_err(hsgen_ctx *ctx, cudaError_t e, const char *what);
 #define HSG_CUDA(ctx, call)                                         \

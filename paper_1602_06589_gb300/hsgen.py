@@ -53,7 +53,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
            "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_autotune",
-           "hsgen_get_stats", "hsgen_last_error",
+           "hsgen_reduce_generalized", "hsgen_get_stats", "hsgen_last_error",
            "hsgen_destroy"]
 
 _LIB = None
@@ -89,6 +89,7 @@ def load(path: Optional[str] = None):
         lib.hsgen_T_matrix.argtypes = [vp, C.c_int, _dp]
         lib.hsgen_depth_layout.argtypes = [vp, _ip, C.c_int]
         lib.hsgen_autotune.argtypes = [vp, C.c_int, vp, vp, vp, C.c_longlong, vp]
+        lib.hsgen_reduce_generalized.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
         lib.hsgen_get_stats.argtypes = [vp, C.POINTER(Stats)]
         lib.hsgen_last_error.argtypes = [vp]
         lib.hsgen_last_error.restype = C.c_char_p
@@ -216,6 +217,12 @@ def hsgen_autotune(ctx, n_g: int, kvec_ptr: int, H_ptr: int, S_ptr: int, ld: int
     _check(ctx, st, "hsgen_autotune")
 
 
+def hsgen_reduce_generalized(ctx, n: int, H_ptr: int, S_ptr: int, ld: int, stream: int = 0):
+    st = load().hsgen_reduce_generalized(ctx, int(n), C.c_void_p(H_ptr), C.c_void_p(S_ptr), int(ld),
+                                         C.c_void_p(stream))
+    _check(ctx, st, "hsgen_reduce_generalized")
+
+
 def hsgen_get_stats(ctx) -> dict:
     s = Stats()
     _check(ctx, load().hsgen_get_stats(ctx, C.byref(s)), "hsgen_get_stats")
@@ -309,6 +316,18 @@ class Generator:
         st = stream if stream is not None else torch.cuda.current_stream(dev)
         hsgen_autotune(self.ctx, n_g, kv.data_ptr(), H.data_ptr(), S.data_ptr(), n_g, st.cuda_stream)
         return H.mT, S.mT
+
+    def reduce(self, H, S, stream=None):
+        """Reduces H c = eps S c to standard form in place (hsgen_reduce_generalized).
+        H, S: the (column-major) complex128 cuda tensors build() returns, or any
+        n x n ones in that layout; returns (H~, factor) as the same views."""
+        import torch
+        n = int(H.shape[0])
+        Hr, Sr = H.mT, S.mT  # the row-major buffers the library sees column-major
+        assert Hr.is_contiguous() and Sr.is_contiguous(), "H, S must be column-major views of contiguous buffers"
+        st = stream if stream is not None else torch.cuda.current_stream(H.device)
+        hsgen_reduce_generalized(self.ctx, n, Hr.data_ptr(), Sr.data_ptr(), n, st.cuda_stream)
+        return H, S
 
     def coefficients(self, kvec, stream=None):
         import torch
