@@ -20,9 +20,10 @@ namespace {
 
 // mode 0: the triangle opposite `uplo` takes the conjugate transpose of the
 // `uplo` triangle; mode 1: both triangles take the average (M + M^H) / 2.
-// Diagonal imaginary parts become 0. One thread per (i, j) with i < j in
-// 32 x 32 tiles staged through shared memory, so both sides read and write
-// columns contiguously.
+// Diagonal imaginary parts become 0. A block takes the tile pair (bi, bj),
+// (bj, bi) with bi <= bj: both tiles are read column-contiguously into shared
+// memory, then each thread writes one (i, j), i <= j, and its mirror (the
+// mirrored writes are strided; the solves around this dominate the time).
 __global__ void hermitian_kernel(int n, double2 *M, long long ld, int uplo, int mode) {
   __shared__ double2 a[32][33], b[32][33];
   const int bi = blockIdx.y, bj = blockIdx.x;  // tile rows bi*32.., columns bj*32.., bi <= bj
@@ -89,6 +90,7 @@ extern "C" hsgen_status hsgen_reduce_generalized(hsgen_ctx *ctx, int n, void *H,
   if (n == 0) return HSGEN_OK;
   if (!H || !S) return set_err(ctx, HSGEN_EINVAL, "reduce: NULL pointer");
   if (ld < n) return set_err(ctx, HSGEN_EINVAL, "reduce: ld < n");
+  if (ld > 0x7fffffffLL) return set_err(ctx, HSGEN_EINVAL, "reduce: ld above the 32-bit range of the solver");
   if (H == S) return set_err(ctx, HSGEN_EINVAL, "reduce: H and S alias");
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
   if (!is_device_ptr(H) || !is_device_ptr(S))
@@ -126,7 +128,6 @@ extern "C" hsgen_status hsgen_reduce_generalized(hsgen_ctx *ctx, int n, void *H,
   if (st != HSGEN_OK) return st;
   cuDoubleComplex *work = (cuDoubleComplex *)ctx->ws_red.ptr;
   int *d_info = (int *)((char *)ctx->ws_red.ptr + work_bytes);
-  if (ld > 0x7fffffffLL) return set_err(ctx, HSGEN_EINVAL, "reduce: ld above the 32-bit range of the solver");
 
   // H in full (only its `uplo` triangle is read), then S = U^H U (or L L^H)
   HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 0, s));
