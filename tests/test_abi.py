@@ -77,3 +77,25 @@ def test_missing_library_fails_loudly(tmp_path):
 
     with pytest.raises(RuntimeError, match="no non-CUDA fallback"):
         hsgen.load(str(tmp_path / "libhsgen.so"))
+
+
+def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
+    """include/hsgen.h compiles as C11 (-Wall -Werror -pedantic) and a C program
+    links against libhsgen.so and calls the entry points that need no GPU."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1602_06589_gb300 import build as cbuild
+
+    libdir = os.path.dirname(cbuild.LIB)
+    exe = str(tmp_path / "abi_from_c")
+    src = os.path.join(ROOT, "tests", "c", "abi_from_c.c")
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        src, "-o", exe, "-L", libdir, "-lhsgen", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.stdout, r.stderr)
