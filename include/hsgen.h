@@ -219,7 +219,11 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
  * S's opt.uplo triangle becomes the Cholesky factor (U with S = U^H U for
  * 'U', L with S = L L^H for 'L'; the other triangle is left as it was) and H
  * becomes H~ = U^-H H U^-1 (= L^-1 H L^-H), written in full and exactly
- * Hermitian, so that H~ y = eps y and c = U^-1 y (= L^-H y). Runs on
+ * Hermitian, so that H~ y = eps y and c = U^-1 y (= L^-H y). With
+ * opt.precision HSGEN_SPLIT and the upper triangle the factorization and the
+ * two triangular solves run blocked (256 rows; FP64 diagonal blocks, the
+ * updates as 7-slice BF16 products on the tensor cores, to FP64-level
+ * accuracy); otherwise cuSOLVER ZPOTRF and cuBLAS ZTRSM in FP64. Runs on
  * `cuda_stream` and returns when it is done. HSGEN_ENUMERIC when S is not
  * positive definite (H and S are then overwritten with partial results);
  * HSGEN_EINVAL for host pointers, aliasing or bad sizes. */

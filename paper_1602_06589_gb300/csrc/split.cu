@@ -1024,6 +1024,116 @@ int choose_slices(double target_rel_err, int override_slices) {
   return kMaxSlices;
 }
 
+// ---------------------------------------------------------------------------
+// Generic C (+)= (+-) P^H Q in the split form (used by the eigenproblem
+// reduction): P is K x M, Q is K x N, complex column-major; C is M x N.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GemmWs {
+  __nv_bfloat16 *Psl, *Qsl;
+  int *expP, *expQ;
+  double *neg;
+  int2 *tiles;
+  size_t bytes;
+};
+
+GemmWs gemm_ws_layout(void *base, int M, int N, int K, int slices) {
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t ldk = (size_t)((K + BK - 1) / BK) * BK;
+  const size_t nbm = (M + BMT - 1) / BMT, nbn = (N + BN - 1) / BN;
+  char *b = (char *)base;
+  GemmWs w;
+  size_t o = 0;
+  w.Psl = (__nv_bfloat16 *)(b + o);
+  o += al(sizeof(__nv_bfloat16) * 2 * slices * (size_t)M * ldk);
+  w.Qsl = (__nv_bfloat16 *)(b + o);
+  o += al(sizeof(__nv_bfloat16) * 3 * slices * (size_t)N * ldk);
+  w.expP = (int *)(b + o);
+  o += al(sizeof(int) * (size_t)M);
+  w.expQ = (int *)(b + o);
+  o += al(sizeof(int) * (size_t)N);
+  w.neg = (double *)(b + o);
+  o += al(sizeof(double) * ldk);
+  w.tiles = (int2 *)(b + o);
+  o += al(sizeof(int2) * nbm * nbn);
+  w.bytes = o;
+  return w;
+}
+
+}  // namespace
+
+size_t split_gemm_ws_bytes(int M, int N, int K, int slices) {
+  return gemm_ws_layout(nullptr, M, N, K, slices).bytes;
+}
+
+hsgen_status split_gemm(hsgen_ctx *ctx, int M, int N, int K, const double2 *P, long long ldp, const double2 *Q,
+                        long long ldq, double2 *C, long long ldc, int uplo, bool accumulate, bool negate,
+                        int slices, void *ws, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return HSGEN_OK;
+  if (K <= 0 || ldp < K || ldq < K || ldc < M || slices < 1 || slices > kMaxSlices || (uplo && M != N))
+    return set_err(ctx, HSGEN_EINVAL, "split_gemm: bad sizes");
+  if (!ctx->d_status) {
+    HSG_CUDA(ctx, cudaMalloc(&ctx->d_status, sizeof(int)));
+    HSG_CUDA(ctx, cudaMallocHost(&ctx->h_status, sizeof(int)));
+    HSG_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  }
+  GemmWs w = gemm_ws_layout(ws, M, N, K, slices);
+  const long long ldk = (long long)((K + BK - 1) / BK) * BK;
+  const double *urow = nullptr;
+  if (negate) {
+    std::vector<double> minus(ldk, -1.0);
+    HSG_CUDA(ctx, cudaMemcpyAsync(w.neg, minus.data(), sizeof(double) * ldk, cudaMemcpyHostToDevice, s));
+    urow = w.neg;
+  }
+  // P as the left operand (planes re, im; negated through the row weights), Q as the right (re, im, -re)
+  HSG_LAUNCH(ctx, launch_slice(P, ldp, K, urow, slices, 2, w.Psl, ldk, (long long)M * ldk, w.expP, M, s));
+  HSG_LAUNCH(ctx, launch_slice(Q, ldq, K, nullptr, slices, 3, w.Qsl, ldk, (long long)N * ldk, w.expQ, N, s));
+  std::vector<int2> tl;
+  if (uplo) {
+    tl = tri_tiles(M, uplo, 16);
+  } else {
+    const int nbm = (M + BMT - 1) / BMT, nbn = (N + BN - 1) / BN;
+    for (int b0 = 0; b0 < nbn; b0 += 16)
+      for (int bi = 0; bi < nbm; ++bi)
+        for (int bj = b0; bj < std::min(nbn, b0 + 16); ++bj) tl.push_back(make_int2(bi, bj));
+  }
+  HSG_CUDA(ctx, cudaMemcpyAsync(w.tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, s));
+  GemmParams G;
+  std::memset(&G, 0, sizeof(G));
+  G.s = slices;
+  G.status = ctx->d_status;
+  G.timeout_ns = (unsigned long long)ctx->opt.wait_timeout_ns;
+  GemmProblem &q = G.prob[0];
+  q.M = M;
+  q.N = N;
+  q.K = (int)ldk;
+  q.kb_begin = 0;
+  q.a_pps = 2;
+  q.b_pps = 3;
+  q.a_real = 0;
+  q.uplo = uplo;
+  q.accumulate = accumulate ? 1 : 0;
+  q.F = fixed_point_bits((int)ldk);
+  q.expA = w.expP;
+  q.expB = w.expQ;
+  q.C = C;
+  q.ldc = ldc;
+  q.n_batch = 1;
+  q.nbm = (M + BMT - 1) / BMT;
+  q.nbn = (N + BN - 1) / BN;
+  q.tile_list = w.tiles;
+  q.tile_begin = 0;
+  q.a_nkb = q.b_nkb = (int)(ldk / BK);
+  if (!make_map(&G.mapA[0], w.Psl, q.a_nkb, M, 2LL * slices, BM) ||
+      !make_map(&G.mapB[0], w.Qsl, q.b_nkb, N, 3LL * slices, BN))
+    return set_err(ctx, HSGEN_ECUDA, "split_gemm: cuTensorMapEncodeTiled failed");
+  G.nprob = 1;
+  G.ntiles = (long long)tl.size();
+  HSG_LAUNCH(ctx, launch_gemm(G, s));
+  return HSGEN_OK;
+}
+
 size_t split_workspace_bytes(int n_g, int chunk_depth, int slices) {
   return split_ws_layout(nullptr, n_g, chunk_depth, slices).bytes;
 }

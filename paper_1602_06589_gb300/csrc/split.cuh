@@ -44,5 +44,15 @@ hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s);
 hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec, void *const *H,
                            void *const *S, const long long *ld, cudaStream_t s);
 void split_release(hsgen_ctx *ctx);
+// C (+)= P^H Q, or C (+)= -(P^H Q) with `negate`, in the split form with
+// `slices` slices: P is K x M and Q is K x N (complex column-major, leading
+// dimensions ldp, ldq >= K), C is M x N (ldc >= M). uplo 'U' / 'L' (M == N):
+// only that triangle's tiles and entries, diagonal imaginary parts set to 0;
+// uplo 0: every entry. `ws` holds split_gemm_ws_bytes(M, N, K, slices) and
+// must not be in use by earlier work still pending on another stream.
+size_t split_gemm_ws_bytes(int M, int N, int K, int slices);
+hsgen_status split_gemm(hsgen_ctx *ctx, int M, int N, int K, const double2 *P, long long ldp, const double2 *Q,
+                        long long ldq, double2 *C, long long ldc, int uplo, bool accumulate, bool negate,
+                        int slices, void *ws, cudaStream_t s);
 
 }  // namespace hsg

@@ -1,6 +1,7 @@
 """GPU parity of the generalized-eigenproblem hand-off (Sec. 2.3, Eq.
 matrix_kohnsham) through the C ABI: S = U^H U (or L L^H) in place and
-H~ = U^-H H U^-1 in full, FP64.
+H~ = U^-H H U^-1 in full; FP64 library form and the split form (blocked,
+updates as 7-slice BF16 products, to FP64-level accuracy).
 
 Inputs: the oracle's muffin-tin H, S plus a stand-in for the interstitial
 part (S + I, H + diag(|K_t|^2)) so that S is positive definite, uploaded in
@@ -51,13 +52,18 @@ def to_device(M, uplo):
     return torch.from_numpy(np.ascontiguousarray(T.T)).cuda()
 
 
-@pytest.mark.parametrize("uplo,n_g", [("U", 90), ("L", 90), ("U", 600), ("L", 600)])
-def test_reduce_matches_oracle(hs, uplo, n_g):
+@pytest.mark.parametrize("precision,uplo,n_g", [("FP64", "U", 90), ("FP64", "L", 90), ("FP64", "U", 600),
+                                                ("FP64", "L", 600), ("SPLIT", "U", 90), ("SPLIT", "U", 600),
+                                                ("SPLIT", "U", 1300), ("SPLIT", "L", 600)])
+def test_reduce_matches_oracle(hs, precision, uplo, n_g):
+    """FP64: cuSOLVER / cuBLAS. SPLIT (upper triangle): blocks of 256, FP64
+    diagonal blocks, updates as 7-slice BF16 products on the tensor cores
+    (1, 3 and 6 blocks here); the lower triangle takes the FP64 path."""
     import torch
 
     sysm, H, S = pd_problem(seed=3 + n_g, n_g=n_g)
     Hd, Sd = to_device(H, uplo), to_device(S, uplo)
-    with hs.Generator(sysm, precision=hs.FP64, uplo=uplo) as g:
+    with hs.Generator(sysm, precision=getattr(hs, precision), uplo=uplo) as g:
         hs.hsgen_reduce_generalized(g.ctx, n_g, Hd.data_ptr(), Sd.data_ptr(), n_g, 0)
         torch.cuda.synchronize()
     Hr = Hd.cpu().numpy().T
@@ -114,15 +120,19 @@ def test_reduce_properties_at_3000(hs):
     assert np.linalg.norm(rec_h - Hf[:, cols]) <= tol_h * np.linalg.norm(Hf[:, cols])
 
 
-def test_reduce_rejects_non_positive_definite(hs):
+@pytest.mark.parametrize("precision,n_g", [("FP64", 64), ("SPLIT", 64), ("SPLIT", 700)])
+def test_reduce_rejects_non_positive_definite(hs, precision, n_g):
+    """S indefinite (SPLIT at N_G 700: the failure is in the third block of 256)."""
     import torch
 
-    sysm, H, S = pd_problem(seed=5, n_g=64)
-    S = S - 2.0 * np.eye(64) * np.max(np.abs(S))  # negative definite
+    sysm, H, S = pd_problem(seed=5, n_g=n_g)
+    S[600:, 600:] -= 2.0 * np.eye(n_g - 600) * np.max(np.abs(S)) if n_g > 600 else 0.0
+    if n_g <= 600:
+        S = S - 2.0 * np.eye(n_g) * np.max(np.abs(S))  # negative definite
     Hd, Sd = to_device(H, "U"), to_device(S, "U")
-    with hs.Generator(sysm, precision=hs.FP64) as g:
+    with hs.Generator(sysm, precision=getattr(hs, precision)) as g:
         with pytest.raises(hs.HsgenError) as ei:
-            hs.hsgen_reduce_generalized(g.ctx, 64, Hd.data_ptr(), Sd.data_ptr(), 64, 0)
+            hs.hsgen_reduce_generalized(g.ctx, n_g, Hd.data_ptr(), Sd.data_ptr(), n_g, 0)
         assert ei.value.status == hs.ENUMERIC
         # the context stays usable
         sysm2, H2, S2 = pd_problem(seed=6, n_g=64)
