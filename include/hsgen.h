@@ -37,7 +37,8 @@
  * Threading: one context must not be used by two host threads at once, and
  * calls on one context are ordered (they share device workspaces): issue
  * them on one stream, or synchronise between streams.
- * Environment (tuning only; results do not change): HSGEN_KSEG_BLOCKS, the
+ * Environment (tuning only; results move at the rounding level at most):
+ * HSGEN_KSEG_BLOCKS, the
  * split form's depth segment in 64-deep blocks (read by hsgen_create;
  * hsgen_autotune picks one per shape); HSGEN_BATCH_BYTES, the slice-memory
  * budget of one batched group; HSGEN_REDUCE_BLOCK, the block rows of the
