@@ -38,11 +38,10 @@
  * calls on one context are ordered (they share device workspaces): issue
  * them on one stream, or synchronise between streams.
  * Environment (tuning only; results move at the rounding level at most):
- * HSGEN_KSEG_BLOCKS, the
- * split form's depth segment in 64-deep blocks (read by hsgen_create;
- * hsgen_autotune picks one per shape); HSGEN_BATCH_BYTES, the slice-memory
- * budget of one batched group; HSGEN_REDUCE_BLOCK, the block rows of the
- * split-form hsgen_reduce_generalized (default 256).
+ * HSGEN_KSEG_BLOCKS, the split form's depth segment in 64-deep blocks (read
+ * by hsgen_create; hsgen_autotune picks one per shape); HSGEN_BATCH_BYTES,
+ * the slice-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
+ * block rows of the split-form hsgen_reduce_generalized (default 256).
  */
 #ifndef HSGEN_H
 #define HSGEN_H
