@@ -17,6 +17,12 @@ the max over ranks are only for timing.
 
 --impl reference times the oracle (plain FP64 CPU code) on the host cores on
 a bounded sample of the same workload, extrapolated to one k-point.
+
+Other lines (not the headline): --s-form legendre (S in the m-summed
+Legendre form), --l-nonsph L (T's non-spherical part up to L), --config 3
+(48 k-points in one batched call), --form fp64 (the FP64 form),
+--library-bars (cuBLAS FP64 / FP64-emulated products on the same operands),
+--reduce (the hand-off to the generalized eigensolver on the built H, S).
 """
 from __future__ import annotations
 
