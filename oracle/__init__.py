@@ -16,6 +16,7 @@ from .hsref import (  # noqa: F401
     coefficients,
     build_HS,
     HS_entries,
+    HS_columns,
     HS_brute,
     threads,
 )

@@ -240,7 +240,7 @@ int hsref_T(const hsref_type *ty, double *T) {
 /*  A_{L,a,t} = 4 pi/(W_l sqrt(Omega)) i^l e^{i K_t.x_a} Y*_L(R_a K^_t)     */
 /*              [u_dot K j_l'(R K) - u_dot' j_l(R K)]                        */
 /*  B_{L,a,t} = same prefactor [-u K j_l'(R K) + u' j_l(R K)]               */
-/*  W_l = u_dot u' - u u_dot'.                                              */
+/*  W_l = u_dot u' - u u_dot' (or the caller's W_l when one is given).      */
 /* ------------------------------------------------------------------------ */
 static void coef_column(const hsref_system *sys, int atom, const double *K, double complex *w) {
   const hsref_type *ty = &sys->types[sys->type_of_atom[atom]];
@@ -262,7 +262,7 @@ static void coef_column(const hsref_system *sys, int atom, const double *K, doub
   double kx = K[0] * x[0] + K[1] * x[1] + K[2] * x[2];
   double complex phase = cos(kx) + I * sin(kx);
   for (int l = 0; l <= lmax; ++l) {
-    double W = ty->udot[l] * ty->du[l] - ty->u[l] * ty->dudot[l];
+    double W = ty->wronskian ? ty->wronskian[l] : ty->udot[l] * ty->du[l] - ty->u[l] * ty->dudot[l];
     double fa = ty->udot[l] * kn * djl[l] - ty->dudot[l] * jl[l];
     double fb = -ty->u[l] * kn * djl[l] + ty->du[l] * jl[l];
     double complex il = (l % 4 == 0) ? 1.0 : (l % 4 == 1) ? I : (l % 4 == 2) ? -1.0 : -I;
@@ -449,6 +449,56 @@ int hsref_HS_entries(const hsref_system *sys, int n_g, const double *kvec, int n
     Sc[p] = cdot(w + (size_t)a * D, y + (size_t)b * D, D, compensated);
   }
   free(w); free(x); free(y); free(slot); free(cols_u);
+  free_layout(sys, &lay);
+  return 0;
+}
+
+static double cnorm(const double complex *p, int n) {
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s += creal(p[k]) * creal(p[k]) + cimag(p[k]) * cimag(p[k]);
+  return sqrt(s);
+}
+
+int hsref_HS_columns(const hsref_system *sys, int n_g, const double *kvec, int n_cols, const int *cols,
+                     double *H, double *S, double *wnorm, double *xnorm, double *ynorm) {
+  if (n_g < 0 || n_cols < 0) return 1;
+  for (int c = 0; c < n_cols; ++c)
+    if (cols[c] < 0 || cols[c] >= n_g) return 1;
+  layout_t lay = {0};
+  if (make_layout(sys, &lay)) {
+    free_layout(sys, &lay);
+    return 2;
+  }
+  int D = lay.depth;
+  /* W for every plane wave (the rows), X = T W and Y = U W for the columns */
+  double complex *w = (double complex *)malloc(sizeof(double complex) * (size_t)D * (n_g + 1));
+  double complex *wc = (double complex *)malloc(sizeof(double complex) * (size_t)D * (n_cols + 1));
+  double complex *x = (double complex *)malloc(sizeof(double complex) * (size_t)D * (n_cols + 1));
+  double complex *y = (double complex *)malloc(sizeof(double complex) * (size_t)D * (n_cols + 1));
+  if (!w || !wc || !x || !y) {
+    free(w); free(wc); free(x); free(y);
+    free_layout(sys, &lay);
+    return 2;
+  }
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int t = 0; t < n_g; ++t)
+    for (int a = 0; a < sys->n_atoms; ++a) coef_column(sys, a, kvec + 3 * t, w + (size_t)t * D + lay.off[a]);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < n_cols; ++c)
+    wxy_column(sys, &lay, kvec + 3 * cols[c], wc + (size_t)c * D, x + (size_t)c * D, y + (size_t)c * D);
+  double complex *Hc = (double complex *)H, *Sc = (double complex *)S;
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < (long long)n_g * n_cols; ++e) {
+    int tp = (int)(e % n_g), c = (int)(e / n_g);
+    Hc[e] = cdot(w + (size_t)tp * D, x + (size_t)c * D, D, 0);
+    Sc[e] = cdot(w + (size_t)tp * D, y + (size_t)c * D, D, 0);
+  }
+  for (int t = 0; t < n_g && wnorm; ++t) wnorm[t] = cnorm(w + (size_t)t * D, D);
+  for (int c = 0; c < n_cols; ++c) {
+    if (xnorm) xnorm[c] = cnorm(x + (size_t)c * D, D);
+    if (ynorm) ynorm[c] = cnorm(y + (size_t)c * D, D);
+  }
+  free(w); free(wc); free(x); free(y);
   free_layout(sys, &lay);
   return 0;
 }

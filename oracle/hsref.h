@@ -37,6 +37,8 @@ typedef struct {
   int lmax_nonsph;          /* l_nonsph (Sec. 3.1, Fig. Tmat_structure): the */
                             /* Gaunt sum enters T only for l, l' <= l_nonsph */
                             /* (l_nonsph >= lmax: everywhere)                */
+  const double *wronskian;  /* NULL, or [lmax+1] W_l given by the caller and */
+                            /* used in App. A.1's prefactor as it is          */
 } hsref_type;
 
 typedef struct {
@@ -69,6 +71,13 @@ int hsref_build_HS(const hsref_system *sys, int n_g, const double *kvec, double 
 /* Entries H[rows[p], cols[p]] and S[...] only. */
 int hsref_HS_entries(const hsref_system *sys, int n_g, const double *kvec, int n_pairs,
                      const int *rows, const int *cols, double *H, double *S, int compensated);
+/* Whole columns: H[:, cols[c]] and S[:, cols[c]] for every row 0..n_g-1
+ * (H, S: n_g x n_cols, column-major, leading dimension n_g). Optional
+ * (NULL to skip): wnorm[n_g] = ||w_t|| of every row's coefficient column,
+ * xnorm[n_cols] = ||T w|| and ynorm[n_cols] = ||U w|| of the chosen columns
+ * (the Cauchy-Schwarz scales of an entry's dot product). */
+int hsref_HS_columns(const hsref_system *sys, int n_g, const double *kvec, int n_cols, const int *cols,
+                     double *H, double *S, double *wnorm, double *xnorm, double *ynorm);
 /* The quadruple sum of Eq. def_hamilton / def_overlap with no intermediate
  * product (tiny inputs only). */
 int hsref_HS_brute(const hsref_system *sys, int n_g, const double *kvec, double *H, double *S,

@@ -26,7 +26,7 @@ class _Type(C.Structure):
                 ("u", _dp), ("du", _dp), ("udot", _dp), ("dudot", _dp),
                 ("udot_norm2", _dp), ("e_l", _dp),
                 ("I_uu", _dp), ("I_uud", _dp), ("I_udu", _dp), ("I_udud", _dp),
-                ("T_override", _dp), ("lmax_nonsph", C.c_int)]
+                ("T_override", _dp), ("lmax_nonsph", C.c_int), ("wronskian", _dp)]
 
 
 class _System(C.Structure):
@@ -46,6 +46,7 @@ def _bind(path: str):
     lib.hsref_coefficients.argtypes = [C.POINTER(_System), C.c_int, C.c_int, _dp, _dp]
     lib.hsref_build_HS.argtypes = [C.POINTER(_System), C.c_int, _dp, _dp, _dp, C.c_longlong, C.c_int, C.c_int]
     lib.hsref_HS_entries.argtypes = [C.POINTER(_System), C.c_int, _dp, C.c_int, _ip, _ip, _dp, _dp, C.c_int]
+    lib.hsref_HS_columns.argtypes = [C.POINTER(_System), C.c_int, _dp, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp]
     lib.hsref_HS_brute.argtypes = [C.POINTER(_System), C.c_int, _dp, _dp, _dp, C.c_longlong]
     lib.hsref_threads.restype = C.c_int
     return lib
@@ -106,6 +107,13 @@ class _Marshal:
                 types[i].T_override = _d(tov)
             else:
                 types[i].T_override = None
+            wr = getattr(t, "wronskian", None)
+            if wr is not None:
+                wa = _f64(wr).copy()
+                self.keep.append(wa)
+                types[i].wronskian = _d(wa)
+            else:
+                types[i].wronskian = None
         self.types = types
         self.toa = np.ascontiguousarray(sysm.type_of_atom, dtype=np.int32)
         self.pos = _f64(sysm.pos).reshape(-1).copy()
@@ -197,6 +205,25 @@ def HS_entries(sysm, kvec: np.ndarray, rows, cols, compensated: bool = False):
     if rc != 0:
         raise RuntimeError(f"hsref_HS_entries failed ({rc})")
     return H.view(np.complex128), S.view(np.complex128)
+
+
+def HS_columns(sysm, kvec: np.ndarray, cols, norms: bool = False):
+    """Whole columns H[:, cols], S[:, cols] (N_G x len(cols) complex), every row.
+    norms=True also returns (||w_t|| for every row, ||T w|| and ||U w|| of the columns)."""
+    m = _Marshal(sysm)
+    kv = _f64(kvec).reshape(-1).copy()
+    n_g = kv.shape[0] // 3
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    H = np.zeros(2 * n_g * c.shape[0])
+    S = np.zeros(2 * n_g * c.shape[0])
+    wn, xn, yn = np.zeros(n_g), np.zeros(c.shape[0]), np.zeros(c.shape[0])
+    rc = load().hsref_HS_columns(m.ptr, n_g, _d(kv), int(c.shape[0]), c.ctypes.data_as(_ip), _d(H), _d(S),
+                                 _d(wn), _d(xn), _d(yn))
+    if rc != 0:
+        raise RuntimeError(f"hsref_HS_columns failed ({rc})")
+    Hc = H.view(np.complex128).reshape(n_g, c.shape[0], order="F")
+    Sc = S.view(np.complex128).reshape(n_g, c.shape[0], order="F")
+    return (Hc, Sc, (wn, xn, yn)) if norms else (Hc, Sc)
 
 
 def HS_brute(sysm, kvec: np.ndarray):

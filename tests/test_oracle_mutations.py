@@ -58,8 +58,13 @@ MUTATIONS = {
     "1/Omega instead of 1/sqrt(Omega)": (
         "4.0 * M_PI / (W * sqrt(sys->omega))", "4.0 * M_PI / (W * sys->omega)"),
     "Wronskian sign": (
-        "double W = ty->udot[l] * ty->du[l] - ty->u[l] * ty->dudot[l];",
-        "double W = ty->u[l] * ty->dudot[l] - ty->udot[l] * ty->du[l];"),
+        ": ty->udot[l] * ty->du[l] - ty->u[l] * ty->dudot[l];",
+        ": ty->u[l] * ty->dudot[l] - ty->udot[l] * ty->du[l];"),
+    "caller's Wronskian ignored": (
+        "double W = ty->wronskian ? ty->wronskian[l] :", "double W = 0 ? ty->wronskian[l] :"),
+    "whole columns: S column from X": (
+        "Sc[e] = cdot(w + (size_t)tp * D, y + (size_t)c * D, D, 0);",
+        "Sc[e] = cdot(w + (size_t)tp * D, x + (size_t)c * D, D, 0);"),
     "l_nonsph cutoff on one index only": (
         "lpp <= l + lp && l <= lns && lp <= lns; ++lpp", "lpp <= l + lp && l <= lns; ++lpp"),
     "conjugate on the wrong side of the dot": (
@@ -81,6 +86,8 @@ PINS = [
     lambda: P.test_H_rank_one_T(),
     lambda: P.test_hermitian_psd_and_brute_force_c0(),
     lambda: P.test_invariances(),
+    lambda: P.test_caller_wronskian(),
+    lambda: P.test_whole_columns_match_full_matrix(),
 ]
 
 

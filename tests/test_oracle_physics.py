@@ -319,6 +319,45 @@ def test_upper_triangle_matches_full():
     assert np.array_equal(He, Hf[rows, cols]) and np.array_equal(Se, Sf[rows, cols])
 
 
+def test_whole_columns_match_full_matrix():
+    """Whole columns (every row) equal the same columns of the full matrix."""
+    sysm = small_system(lmax=3, n_atoms=3, seed=37)
+    kv = kpoint_list(sysm.lattice, (0.17, -0.05, 0.29), 50)
+    Hf, Sf = oracle.build_HS(sysm, kv, full=True)
+    cols = [0, 17, 49]
+    Hc, Sc = oracle.HS_columns(sysm, kv, cols)
+    assert np.array_equal(Hc, Hf[:, cols]) and np.array_equal(Sc, Sf[:, cols])
+
+
+def test_caller_wronskian():
+    """App. A.1 divides A and B by W_l: a caller's W_l equal to
+    u_dot u' - u u_dot' changes nothing, and W_l scaled by c_l scales the A
+    and B rows of that l by 1 / c_l."""
+    sysm = small_system(lmax=4, n_atoms=3, seed=31)
+    kv = kpoint_list(sysm.lattice, (0.11, 0.23, -0.17), 30)
+    W0 = [oracle.coefficients(sysm, a, kv) for a in range(sysm.n_atoms)]
+    same = copy.deepcopy(sysm)
+    for ty in same.types:
+        ty.wronskian = ty.udot * ty.du - ty.u * ty.dudot
+    for a in range(sysm.n_atoms):
+        assert np.array_equal(oracle.coefficients(same, a, kv), W0[a])
+    scaled = copy.deepcopy(sysm)
+    rng = np.random.default_rng(7)
+    cs = []
+    for ty in scaled.types:
+        c = rng.uniform(0.5, 2.0, ty.lmax + 1)
+        ty.wronskian = c * (ty.udot * ty.du - ty.u * ty.dudot)
+        cs.append(c)
+    for a in range(sysm.n_atoms):
+        t = int(sysm.type_of_atom[a])
+        ty = sysm.types[t]
+        lvec = np.repeat(np.arange(ty.lmax + 1), 2 * np.arange(ty.lmax + 1) + 1)
+        inv = np.concatenate([1.0 / cs[t][lvec], 1.0 / cs[t][lvec]])
+        W1 = oracle.coefficients(scaled, a, kv)
+        assert np.max(np.abs(W1 - W0[a] * inv[:, None])) <= 1e-14 * np.max(np.abs(W0[a]))
+        assert not np.allclose(W1, W0[a])
+
+
 def test_invariances():
     sysm = small_system(lmax=3, n_atoms=4, seed=29)
     kv = kpoint_list(sysm.lattice, (0.1, -0.2, 0.35), 45)

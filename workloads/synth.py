@@ -61,6 +61,9 @@ class AtomType:
     # l_nonsph: the non-spherical (Gaunt) part of T is dense for l, l' <= it;
     # None means l_max (Sec. 3.1, Fig. Tmat_structure)
     lmax_nonsph: Optional[int] = None
+    # W_l given by the caller ((l_max+1,) floats), or None: computed from the
+    # boundary values as u_dot u' - u u_dot' (App. A.1)
+    wronskian: Optional[np.ndarray] = None
 
     @property
     def nl(self) -> int:
