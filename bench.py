@@ -122,6 +122,54 @@ def _traffic(config: int):
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
+# whole columns of the triangle compared with the oracle after the timed
+# region: tile (64 / 128 columns) and band (1024 columns) edges, an interior
+# column and the last one (the ragged tail); every row block is covered
+ERROR_COLS = (0, 127, 1024, 10111, -1)
+
+
+def error_columns(n):
+    return sorted({c % n for c in ERROR_COLS if -n <= c < n})
+
+
+def oracle_columns(system, kvec, cols):
+    """The oracle's whole columns of H and S, with the per-entry scales."""
+    import oracle
+
+    t0 = time.perf_counter()
+    Ho, So, norms = oracle.HS_columns(system, kvec, cols, norms=True)
+    return {"cols": cols, "H": Ho, "S": So, "norms": norms, "seconds": time.perf_counter() - t0}
+
+
+def column_errors(Hc, Sc, ref, uplo="U"):
+    """Relative Frobenius error and the largest normwise per-entry error
+    |dX_ij| / (||w_i|| ||x_j||) over the written triangle of the columns."""
+    import numpy as np
+
+    wn, xn, yn = ref["norms"]
+    out = {}
+    for name, A, B, sc in (("H", Hc, ref["H"], xn), ("S", Sc, ref["S"], yn)):
+        d2 = b2 = per = 0.0
+        for k, j in enumerate(ref["cols"]):
+            rows = slice(0, j + 1) if uplo == "U" else slice(j, None)
+            a, b = A[rows, k], B[rows, k]
+            d2 += float(np.sum(np.abs(a - b) ** 2))
+            b2 += float(np.sum(np.abs(b) ** 2))
+            per = max(per, float(np.max(np.abs(a - b) / (wn[rows] * sc[k]))))
+        out[name] = {"rel_frobenius": (d2 / b2) ** 0.5, "max_entry_normwise": per}
+    return out
+
+
+def _fp64_peak():
+    """Measured FP64 DMMA peak (mma.sync.m8n8k4.f64 loop on this GPU model), if recorded."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_dmma_peak_GB300.json")) as f:
+            rec = json.load(f)
+        return float(rec["tflops"]), float(rec.get("sm_mhz", 0.0)) or None
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
 def oracle_sample_time(system, kvec, m: int):
     """Oracle cost model from two bounded samples on the host cores:
     m columns with m diagonal entries (column cost), then all m^2 pairs."""
@@ -482,6 +530,44 @@ def library_bars(args, w):
     print(json.dumps(out), flush=True)
 
 
+def roofline(st, f_contract, c_ms, precision, peaks, clk_s, args, hsgen):
+    """Roofline of the dominant kernel (the H/S contraction) from the library's
+    own CUDA events. Split form: executed BF16 products per second against the
+    measured cuBLAS BF16 GEMM peak; `frac` scales that peak to the SM clock
+    sampled during this run (the peak was taken at its own median clock under
+    the power cap), `frac_vs_measured_peak` is the unscaled ratio. FP64 form:
+    algorithmic FP64 flops per second against the measured FP64 DMMA peak."""
+    mhz = clk_s["sm_mhz"] if clk_s else None
+    if precision == hsgen.SPLIT:
+        scheme = st.get("scheme", 0)
+        units = st.get("products", 0) or st["slices"] * (st["slices"] + 1) // 2
+        lp_flops = f_contract * units  # bf16 products actually executed
+        achieved = lp_flops / (c_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        pmhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+        peak_clk = peak * mhz / pmhz if (mhz and pmhz) else peak
+        return {"bound": "tensor", "achieved": achieved, "peak": peak_clk, "unit": "TFLOP/s",
+                "frac": achieved / peak_clk, "frac_vs_measured_peak": achieved / peak,
+                "measured_peak": peak, "measured_peak_mhz": pmhz, "run_mhz": mhz,
+                "bf16_products_per_fp64_mac": units,
+                "traffic": _traffic(args.config) if not args.n_g and st.get("s_form") != hsgen.S_LEGENDRE else None,
+                "traffic_unit": "DRAM bytes per H/S depth-segment launch (ncu, 1 pass)",
+                "kernel": "split H/S contraction (tcgen05 bf16)",
+                "peak_source": ("measured bf16 sustained (MEASURED_PEAKS.json), scaled to the sampled SM clock"
+                                if "bf16_tflops_sustained" in peaks else "fallback")}
+    achieved = f_contract / (c_ms * 1e-3) / 1e12
+    p64, p64_mhz = _fp64_peak()
+    if p64:
+        peak = p64 * mhz / p64_mhz if (mhz and p64_mhz) else p64
+        src = "measured FP64 DMMA loop (profiles/fp64_dmma_peak_GB300.json)" + (", scaled to the sampled SM clock"
+                                                                              if (mhz and p64_mhz) else "")
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0
+        src = "measured bf16 sustained x nominal fp64/bf16 ratio"
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "run_mhz": mhz, "traffic": None, "kernel": "FP64 H/S contraction (mma.sync f64)", "peak_source": src}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -495,8 +581,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-columns", type=int, default=384)
     ap.add_argument("--n-g", type=int, default=0, help="override N_G (smaller cases for profiling)")
-    ap.add_argument("--fp64-compare", action="store_true",
-                    help="also time one FP64-form step on the same workload")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the FP64-form step timed after the split form on the same workload")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the comparison of whole columns of H and S with the oracle")
     ap.add_argument("--l-nonsph", type=int, default=-1,
                     help="l_nonsph of every species (default: l_max, a dense T)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -613,23 +701,8 @@ def main():
         f_contract = fl.algorithmic_flops(n, nlc)["F_HS"] / 2
     else:
         f_contract = fal["F_HS"]
-    if precision == hsgen.SPLIT:
-        slices = st["slices"]
-        lp_flops = f_contract * slices * (slices + 1) / 2  # bf16 products actually executed
-        achieved = lp_flops / (c_ms * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic(args.config) if not args.n_g and st.get("s_form") != hsgen.S_LEGENDRE else None,
-                "traffic_unit": "DRAM bytes per H/S depth-segment launch (ncu, 1 pass)",
-                "kernel": "split H/S contraction (tcgen05 bf16)",
-                "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback"}
-    else:
-        achieved = f_contract / (c_ms * 1e-3) / 1e12
-        # FP64 tensor peak: measured bf16 sustained x nominal FP64/bf16 ratio (1.25 / 2250)
-        peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "FP64 H/S contraction (mma.sync f64)",
-                "peak_source": "measured bf16 sustained x nominal fp64/bf16 ratio"}
+    clk_s = clk.summary()
+    roof = roofline(st, f_contract, c_ms, precision, peaks, clk_s, args, hsgen)
 
     line = {
         "metric": METRIC, "value": s_per_k, "unit": "s/k-point", "n_gpus": world, "steps": args.steps,
@@ -648,21 +721,8 @@ def main():
         "phases_ms": {k: st[k] for k in ("ms_coefficients", "ms_tapply", "ms_slice", "ms_contract", "ms_s", "ms_total")},
         "roofline": roof, "gpu_launches": launches,
     }
-    clk_s = clk.summary()
     if clk_s:
         line["clocks"] = clk_s
-
-    if args.fp64_compare and precision == hsgen.SPLIT and rank == 0:
-        g64 = hsgen.Generator(sysm, device=local, precision=hsgen.FP64)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g64.build(kv, H, S)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t64 = e0.elapsed_time(e1) * 1e-3
-        line["fp64_form"] = {"s_per_kpoint": t64, "eff_tflops": fal["total"] / t64 / 1e12, "steps": 1}
-        g64.close()
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -694,6 +754,46 @@ def main():
                        "upload_ms": [round(x, 1) for x in up_ms], "download_ms": [round(x, 1) for x in down_ms]}
         del Hh, Sh
 
+    # accuracy of the timed build (after the timed region): whole columns vs the oracle
+    ref = None
+    if rank == 0 and not args.no_error and st.get("s_form") != hsgen.S_LEGENDRE and args.l_nonsph < 0:
+        cols = error_columns(n)
+        ci = torch.tensor(cols, device=dev)
+        Hc, Sc = H.mT[:, ci].cpu().numpy(), S.mT[:, ci].cpu().numpy()
+        ref = oracle_columns(sysm, kv_host, cols)
+        line["error"] = dict(column_errors(Hc, Sc, ref), tolerance=1e-11 if precision == hsgen.SPLIT else 1e-12,
+                             sample=f"{len(cols)} whole columns {cols} (all rows of the upper triangle) vs the "
+                                    f"oracle ({ref['seconds']:.0f} s on the host cores)")
+    g.close()
+
+    if rank == 0 and precision == hsgen.SPLIT and not args.no_fp64_compare:
+        # the plain form on the same workload: one timed FP64 build (after a
+        # small build that loads its kernels), with its own error
+        g64 = hsgen.Generator(sysm, device=local, precision=hsgen.FP64, s_form=s_form)
+        g64.build(kv[:64])
+        H.zero_()
+        S.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk64:
+            e0.record(stream)
+            g64.build(kv, H, S)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) * 1e-3
+        st64 = g64.stats()
+        f64 = {"s_per_kpoint": t64, "eff_tflops": fal["total"] / t64 / 1e12, "steps": 1, "warmup": 0,
+               "phases_ms": {k: st64[k] for k in ("ms_coefficients", "ms_tapply", "ms_contract", "ms_total")},
+               "roofline": roofline(st64, f_contract, st64["ms_contract"], hsgen.FP64, peaks, clk64.summary(),
+                                    args, hsgen),
+               "split_speedup": t64 / s_per_k}
+        if ref is not None:
+            ci = torch.tensor(ref["cols"], device=dev)
+            Hc, Sc = H.mT[:, ci].cpu().numpy(), S.mT[:, ci].cpu().numpy()
+            f64["error"] = dict(column_errors(Hc, Sc, ref), tolerance=1e-12)
+        line["fp64_form"] = f64
+        g64.close()
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
 
@@ -701,7 +801,6 @@ def main():
         line["cpu_baseline"] = {"value": full, "unit": "s/k-point", "cores": oracle.threads(), "kind": "oracle",
                                 "sample": f"{args.ref_columns} columns + {args.ref_columns ** 2} entries "
                                           f"({spent:.1f} s of CPU work), extrapolated to the full k-point"}
-    g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -37,11 +37,15 @@
  * Threading: one context must not be used by two host threads at once, and
  * calls on one context are ordered (they share device workspaces): issue
  * them on one stream, or synchronise between streams.
+ * Buffers on another GPU than the context's are rejected (HSGEN_EINVAL).
  * Environment (tuning only; results move at the rounding level at most):
  * HSGEN_KSEG_BLOCKS, the split form's depth segment in 64-deep blocks (read
  * by hsgen_create; hsgen_autotune picks one per shape); HSGEN_BATCH_BYTES,
  * the slice-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
  * block rows of the split-form hsgen_reduce_generalized (default 256).
+ * Fault injection (tests): HSGEN_FAIL_ALLOC=1 makes every growth of a
+ * library workspace fail as an out-of-memory cudaMalloc would (the call
+ * returns HSGEN_ENOMEM; the context stays usable once the variable is unset).
  */
 #ifndef HSGEN_H
 #define HSGEN_H
@@ -153,14 +157,21 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
  * K_t = k + G_t (host or device pointer). H and S are complex128 column-major
  * n_g x n_g with leading dimension ld >= n_g: device pointers (written on
  * `cuda_stream`, a cudaStream_t or NULL for the default stream; only the
- * triangle named by opt.uplo is written unless opt.fill_full; the FP64 form
- * returns without waiting, the split form waits for the stream so that it
- * can read the status word of its bounded waits and report HSGEN_ETIMEOUT
- * from this call) or host pointers (computed in a library-owned device buffer
- * and copied back in full, ld x n_g entries: the other triangle is zero
- * unless opt.fill_full; the call returns after the copy; in the split form
- * the copies of finished column bands run on a library-owned stream while
- * the last tiles are computed). Diagonal imaginary parts are set to 0. */
+ * triangle named by opt.uplo is written unless opt.fill_full; with a device
+ * kvec the call returns without waiting for the device, in both forms) or
+ * host pointers (computed in a library-owned device buffer and copied back in
+ * full, ld x n_g entries: the other triangle is zero unless opt.fill_full;
+ * the call returns after the copy; in the split form the copies of finished
+ * column bands run on a library-owned stream while the last tiles are
+ * computed). Diagonal imaginary parts are set to 0.
+ * Bounded waits (split form): every device-side wait of the tensor-core
+ * kernels gives up after opt.wait_timeout_ns and records it in a status word
+ * instead of trapping. A call that returns before its work is done cannot see
+ * that word; it is read, and HSGEN_ETIMEOUT returned (the results of the call
+ * that launched the expired wait are then invalid), by hsgen_synchronize, by
+ * hsgen_get_stats, by this call itself when it waits (host inputs or
+ * outputs), and by the next build or reduction on the context once the
+ * earlier work has finished. */
 hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);
 
@@ -184,12 +195,16 @@ hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, voi
  * cudaMalloc to grow its workspace, this function never does (nor cudaFree,
  * nor any allocating routine). Its scratch (the radial factors) is a fixed
  * 16 MiB array in device memory that belongs to the loaded library and is
- * held on every GPU that loads it until the process exits; it limits
- * n_types * n_g to 95325, larger requests return HSGEN_EINVAL without
- * launching anything. kvec and W must be device pointers (HSGEN_EINVAL
- * otherwise); the call is asynchronous on `cuda_stream`. The first call on a
- * device looks up the array's device address (once per device); make that
- * first call before capturing the stream into a graph. All calls, from every
+ * held on every GPU that uses it until the process exits (under the CUDA
+ * runtime's default lazy loading the 16 MiB are taken on a device at the
+ * first call of this function there, not when the library is loaded); it
+ * limits n_types * n_g to 95325, larger requests return HSGEN_EINVAL without
+ * launching anything. kvec and W must be device pointers on the context's
+ * GPU (HSGEN_EINVAL otherwise); the call is asynchronous on `cuda_stream`.
+ * The first call on a device looks up the array's device address (once per
+ * device, again after that device's context was replaced, e.g. by
+ * cudaDeviceReset); make that first call before capturing the stream into a
+ * graph. All calls, from every
  * context, share the one array: calls whose kernels overlap on the GPU (on
  * different streams, or from different host threads) race and must be
  * ordered by the caller. Nothing needs clearing between calls: every entry
@@ -230,11 +245,20 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
  * updates as 7-slice BF16 products on the tensor cores, to FP64-level
  * accuracy); otherwise cuSOLVER ZPOTRF and cuBLAS ZTRSM in FP64. Runs on
  * `cuda_stream` and returns when it is done. HSGEN_ENUMERIC when S is not
- * positive definite (H and S are then overwritten with partial results);
+ * positive definite: the leading minor that failed is named in
+ * hsgen_last_error, and H and S are then overwritten with partial results
+ * (the call still runs to its end, so both must be rebuilt);
  * HSGEN_EINVAL for host pointers, aliasing or bad sizes. */
 hsgen_status hsgen_reduce_generalized(hsgen_ctx *ctx, int n, void *H, void *S, long long ld, void *cuda_stream);
 
+/* Statistics of the last call (waits for its device work). Returns
+ * HSGEN_ETIMEOUT, with the stats filled in all the same, when a bounded wait
+ * of an earlier split-form call expired (see hsgen_build_HS). */
 hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *stats);
+/* Waits for `cuda_stream` and reports the bounded-wait status of the split
+ * form's work queued on it: HSGEN_ETIMEOUT when a wait expired since the last
+ * report (no counterpart in the paper). */
+hsgen_status hsgen_synchronize(hsgen_ctx *ctx, void *cuda_stream);
 const char *hsgen_last_error(const hsgen_ctx *ctx);
 /* Releases the context and its device memory. NULL-safe. */
 void hsgen_destroy(hsgen_ctx *ctx);

@@ -36,6 +36,15 @@ static bool finite_all(const double *p, size_t n) {
   return true;
 }
 
+bool on_other_device(const void *p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device != device;
+}
+
 bool is_device_ptr(const void *p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -58,6 +67,12 @@ static bool is_pinned_host(const void *p) {
 
 hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes) {
   if (w.bytes >= bytes) return HSGEN_OK;
+  // fault injection for tests: HSGEN_FAIL_ALLOC=1 makes every workspace
+  // allocation fail the way an out-of-memory cudaMalloc does (nothing freed,
+  // nothing allocated)
+  if (const char *f = std::getenv("HSGEN_FAIL_ALLOC"))
+    if (std::atoi(f) != 0)
+      return set_err(ctx, HSGEN_ENOMEM, "cudaMalloc(workspace): out of memory (injected by HSGEN_FAIL_ALLOC)");
   if (w.ptr) {
     cudaError_t e = cudaFree(w.ptr);
     w.ptr = nullptr;
@@ -525,6 +540,8 @@ hsgen_status hsgen_coefficients(hsgen_ctx *ctx, int n_g, const double *kvec, voi
     if (st != HSGEN_OK) return st;
   }
   if (!is_device_ptr(W)) return set_err(ctx, HSGEN_EINVAL, "coefficients: W must be a device pointer");
+  if (on_other_device(W, ctx->device) || on_other_device(kvec, ctx->device))
+    return set_err(ctx, HSGEN_EINVAL, "coefficients: a buffer lives on another GPU than the context's");
   WsLayout L = ws_layout(ctx, n_g, 0, false, 0);
   hsgen_status st = ensure_ws(ctx, ctx->ws_main, L.total);
   if (st != HSGEN_OK) return st;
@@ -557,6 +574,11 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   if (ld < n_g) return set_err(ctx, HSGEN_EINVAL, "build_HS: ld < n_g");
   if (H == S) return set_err(ctx, HSGEN_EINVAL, "build_HS: H and S alias");
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  // a bounded wait that expired in an earlier call whose work has finished since
+  hsgen_status pst = split_poll_status(ctx, false);
+  if (pst != HSGEN_OK) return pst;
+  if (on_other_device(kvec, ctx->device) || on_other_device(H, ctx->device) || on_other_device(S, ctx->device))
+    return set_err(ctx, HSGEN_EINVAL, "build_HS: a buffer lives on another GPU than the context's");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   bool kdev = is_device_ptr(kvec);
   if (!kdev) {
@@ -641,11 +663,17 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
     if (!job.copy.S) HSG_CUDA(ctx, cudaMemcpyAsync(S, job.S, hs_bytes, cudaMemcpyDeviceToHost, s));
   }
   if (host_io) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[8], s));
+  // the split form's status word is read later (asynchronous call), except
+  // with host inputs or outputs, where this call waits for its work anyway
   if (split) {
-    st = split_check_status(ctx, s);
+    st = split_post_status(ctx, s);
     if (st != HSGEN_OK) return st;
   }
-  if (!hdev || !kdev) HSG_CUDA(ctx, cudaStreamSynchronize(s));
+  if (!hdev || !kdev) {
+    HSG_CUDA(ctx, cudaStreamSynchronize(s));
+    st = split_poll_status(ctx, true);
+    if (st != HSGEN_OK) return st;
+  }
   ctx->stats.precision = ctx->opt.precision;
   ctx->stats.n_kpoints = 1;
   ctx->stats.flops_algorithmic = algorithmic_flops(ctx, n_g);
@@ -664,7 +692,12 @@ hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, con
   if (n_k < 0 || (n_k > 0 && (!n_g || !kvec || !H || !S || !ld)))
     return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: bad argument");
   double flops = 0.0;
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  hsgen_status pst = split_poll_status(ctx, false);
+  if (pst != HSGEN_OK) return pst;
   for (int k = 0; k < n_k; ++k) {
+    if (n_g[k] > 0 && (on_other_device(H[k], ctx->device) || on_other_device(S[k], ctx->device)))
+      return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: a buffer lives on another GPU than the context's");
     if (n_g[k] > 0 && !is_device_ptr(H[k]))
       return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: H, S must be device pointers");
   }
@@ -711,6 +744,8 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
     st = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
     if (st != HSGEN_OK) return st;
     HSG_CUDA(ctx, cudaStreamSynchronize(s));
+    st = split_poll_status(ctx, true);
+    if (st != HSGEN_OK) return st;
     float t = 0.f;
     HSG_CUDA(ctx, cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[5]));
     ms = t;
@@ -769,7 +804,15 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   st.kseg_blocks = ctx->kseg_blocks;
   st.tile_band = ctx->tile_band;
   *out = st;
-  return HSGEN_OK;
+  // the stats are filled in either way; a wait that expired is reported here
+  return split_poll_status(ctx, true);
+}
+
+hsgen_status hsgen_synchronize(hsgen_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return HSGEN_EINVAL;
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  HSG_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  return split_poll_status(ctx, true);
 }
 
 const char *hsgen_last_error(const hsgen_ctx *ctx) {

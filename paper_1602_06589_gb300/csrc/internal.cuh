@@ -87,6 +87,8 @@ struct hsgen_ctx {
   int split_slices = 0;             // slices the species' T were cut into
   int *d_status = nullptr;          // device status word of the split kernels
   int *h_status = nullptr;          // pinned host copy
+  cudaEvent_t status_ev = nullptr;  // marks the arrival of the latest copy in h_status
+  bool status_pending = false;      // a copy of the status word is queued and not yet read
   void *d_tiles = nullptr;          // split form: tile list of one triangle (int2 row/column blocks)
   int tiles_n = -1, tiles_uplo = 0;
   long long tiles_count = 0;
@@ -113,6 +115,8 @@ namespace hsg {
 // ---- error helpers ---------------------------------------------------------
 // True for device (or managed) memory.
 bool is_device_ptr(const void *p);
+// True for device memory of a GPU other than `device`.
+bool on_other_device(const void *p, int device);
 // Grows a library workspace to at least `bytes` (contents not kept).
 hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes);
 // Frees the reduction's handles and buffers.

@@ -10,12 +10,17 @@
 // entry point takes its scratch from a fixed array in device memory that is
 // part of the loaded library instead.
 //
-// The array below is allocated by the CUDA runtime when the module is loaded
-// on a device and stays there until the process exits, on every GPU that
-// loads the library. Host code cannot use its name as a device address (on
-// the host the name is only a stand-in), so the device address is fetched
-// once per device with cudaGetSymbolAddress, with that device current, during
-// the first call of the entry point on that device.
+// The array below is allocated by the CUDA runtime when the library's device
+// code is loaded into a context on a device (with the runtime's default lazy
+// loading that happens at the first call of this entry point on that device,
+// not when the library is loaded into the process) and stays there until the
+// context ends, normally at process exit, on every GPU that uses it. Host code
+// cannot use its name as a device address (on the host the name is only a
+// stand-in), so the device address is fetched with cudaGetSymbolAddress, with
+// that device current, during the first call on that device, and again after
+// the device's context has been replaced (for example by cudaDeviceReset).
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -31,16 +36,40 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};  // context the address belongs to
 
-// Device address of the scratch array on `device` (set up on first use).
+// Device address of the scratch array on `device`, which must be current
+// (looked up on first use, and again when the device's context changed).
 cudaError_t scratch_address(int device, void **out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[device]) {
+  // the driver's context calls, fetched at run time (the library does not
+  // link the driver library itself)
+  typedef CUresult (*GetCurrentFn)(CUcontext *);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!get_current || !get_id) {
+    void *p1 = nullptr, *p2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    get_current = (GetCurrentFn)p1;
+    get_id = (GetIdFn)p2;
+  }
+  // cudaSetDevice (called before this) has made the device's primary context current
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (!g_scratch_addr[device] || g_scratch_ctx[device] != id) {
     void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[device] = p;
+    g_scratch_ctx[device] = id;
   }
   *out = g_scratch_addr[device];
   return cudaSuccess;
@@ -76,6 +105,8 @@ extern "C" hsgen_status hsgen_coefficients_noalloc(hsgen_ctx *ctx, int n_g, cons
     cudaGetLastError();
     return set_err(ctx, HSGEN_EINVAL, "coefficients_noalloc: W must be a device pointer");
   }
+  if (on_other_device(kvec, ctx->device) || on_other_device(W, ctx->device))
+    return set_err(ctx, HSGEN_EINVAL, "coefficients_noalloc: kvec or W lives on another GPU than the context's");
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
   void *scratch = nullptr;
   HSG_CUDA(ctx, scratch_address(ctx->device, &scratch));

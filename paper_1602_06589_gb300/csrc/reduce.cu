@@ -163,6 +163,10 @@ extern "C" hsgen_status hsgen_reduce_generalized(hsgen_ctx *ctx, int n, void *H,
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
   if (!is_device_ptr(H) || !is_device_ptr(S))
     return set_err(ctx, HSGEN_EINVAL, "reduce: H and S must be device pointers");
+  if (on_other_device(H, ctx->device) || on_other_device(S, ctx->device))
+    return set_err(ctx, HSGEN_EINVAL, "reduce: H or S lives on another GPU than the context's");
+  hsgen_status pst = split_poll_status(ctx, false);  // an earlier build's expired wait
+  if (pst != HSGEN_OK) return pst;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (!ctx->blas) {
     cublasHandle_t h = nullptr;

@@ -1300,17 +1300,45 @@ hsgen_status split_join_copies(hsgen_ctx *ctx, cudaStream_t s) {
   return HSGEN_OK;
 }
 
-hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s) {
+hsgen_status split_post_status(hsgen_ctx *ctx, cudaStream_t s) {
   if (!ctx->d_status) return HSGEN_OK;
+  if (!ctx->status_ev) HSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->status_ev, cudaEventDisableTiming));
   HSG_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HSG_CUDA(ctx, cudaStreamSynchronize(s));
-  int st = *ctx->h_status;
+  HSG_CUDA(ctx, cudaEventRecord(ctx->status_ev, s));
+  ctx->status_pending = true;
+  return HSGEN_OK;
+}
+
+hsgen_status split_poll_status(hsgen_ctx *ctx, bool wait) {
+  if (!ctx->status_pending) return HSGEN_OK;
+  if (wait) {
+    HSG_CUDA(ctx, cudaEventSynchronize(ctx->status_ev));
+  } else {
+    const cudaError_t e = cudaEventQuery(ctx->status_ev);
+    if (e == cudaErrorNotReady) {
+      cudaGetLastError();
+      return HSGEN_OK;
+    }
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaEventQuery(status word)");
+  }
+  ctx->status_pending = false;
+  const int st = *ctx->h_status;
   if (st != 0) {
-    HSG_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+    *ctx->h_status = 0;
+    // error path only: clear the word before any later launch can read it
+    HSG_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+    HSG_CUDA(ctx, cudaDeviceSynchronize());
     return set_err(ctx, HSGEN_ETIMEOUT,
-                   "split kernel: a bounded device wait expired (status " + std::to_string(st) + ")");
+                   "split kernel: a bounded device wait expired (status " + std::to_string(st) +
+                       "); the results of the call that launched it are invalid");
   }
   return HSGEN_OK;
+}
+
+hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s) {
+  hsgen_status st = split_post_status(ctx, s);
+  if (st != HSGEN_OK) return st;
+  return split_poll_status(ctx, true);
 }
 
 // Many k-points (one H, S per k-point, Sec. 2.3): per k-point the cheap steps (radial factors,
@@ -1598,7 +1626,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   ctx->phase_used[2] = 0;
   ctx->phase_used[3] = 0;
   ctx->stats.s_form = leg ? HSGEN_S_LEGENDRE : HSGEN_S_CONTRACTION;
-  return split_check_status(ctx, s);
+  return split_post_status(ctx, s);
 }
 
 void split_release(hsgen_ctx *ctx) {
@@ -1620,6 +1648,9 @@ void split_release(hsgen_ctx *ctx) {
   ctx->copy_stream = nullptr;
   if (ctx->copy_ev) cudaEventDestroy(ctx->copy_ev);
   ctx->copy_ev = nullptr;
+  if (ctx->status_ev) cudaEventDestroy(ctx->status_ev);
+  ctx->status_ev = nullptr;
+  ctx->status_pending = false;
   if (ctx->ws_batch.ptr) cudaFree(ctx->ws_batch.ptr);
   ctx->ws_batch.ptr = nullptr;
   ctx->ws_batch.bytes = 0;

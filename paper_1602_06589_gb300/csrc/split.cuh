@@ -37,7 +37,13 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
                          cudaStream_t s, bool record, const CopyOut *co = nullptr);
 // Makes `s` wait for the copies split_chunk queued on the copy stream.
 hsgen_status split_join_copies(hsgen_ctx *ctx, cudaStream_t s);
-// Reads the device status word of the split launches of this call (bounded waits).
+// The device status word of the split launches (bounded waits): post queues
+// a copy of it behind the work on `s` without waiting; poll reads the latest
+// posted copy (wait: block until it has arrived; otherwise HSGEN_OK while it
+// is still on its way) and returns HSGEN_ETIMEOUT, clearing the word, when a
+// wait expired; check = post + poll with wait.
+hsgen_status split_post_status(hsgen_ctx *ctx, cudaStream_t s);
+hsgen_status split_poll_status(hsgen_ctx *ctx, bool wait);
 hsgen_status split_check_status(hsgen_ctx *ctx, cudaStream_t s);
 // Batched k-points in one persistent launch; HSGEN_ENOTSUP when not applicable
 // (the caller then loops over k-points).

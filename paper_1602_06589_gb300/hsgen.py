@@ -53,7 +53,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
            "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_autotune",
-           "hsgen_reduce_generalized", "hsgen_get_stats", "hsgen_last_error",
+           "hsgen_reduce_generalized", "hsgen_get_stats", "hsgen_synchronize", "hsgen_last_error",
            "hsgen_destroy"]
 
 _LIB = None
@@ -91,6 +91,7 @@ def load(path: Optional[str] = None):
         lib.hsgen_autotune.argtypes = [vp, C.c_int, vp, vp, vp, C.c_longlong, vp]
         lib.hsgen_reduce_generalized.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
         lib.hsgen_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        lib.hsgen_synchronize.argtypes = [vp, vp]
         lib.hsgen_last_error.argtypes = [vp]
         lib.hsgen_last_error.restype = C.c_char_p
         lib.hsgen_destroy.argtypes = [vp]
@@ -229,6 +230,11 @@ def hsgen_get_stats(ctx) -> dict:
     return {k: getattr(s, k) for k, _ in Stats._fields_}
 
 
+def hsgen_synchronize(ctx, stream: int = 0):
+    """Waits for `stream`; raises HsgenError(ETIMEOUT) if a bounded device wait expired."""
+    _check(ctx, load().hsgen_synchronize(ctx, C.c_void_p(stream)), "hsgen_synchronize")
+
+
 def hsgen_destroy(ctx):
     if ctx:
         load().hsgen_destroy(ctx)
@@ -346,3 +352,9 @@ class Generator:
 
     def stats(self) -> dict:
         return hsgen_get_stats(self.ctx)
+
+    def synchronize(self, stream=None):
+        """Waits for the stream and reports an expired bounded wait (HSGEN_ETIMEOUT)."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", self.device))
+        hsgen_synchronize(self.ctx, st.cuda_stream)

@@ -12,6 +12,8 @@ At the 16-atom / N_G 3000 size the library's own H, S are reduced and checked
 through properties that hold at any size (U^H U = S and U^H H~ U = H on
 sampled columns, exact Hermitian symmetry).
 """
+import re
+
 import numpy as np
 import pytest
 
@@ -134,6 +136,9 @@ def test_reduce_rejects_non_positive_definite(hs, precision, n_g):
         with pytest.raises(hs.HsgenError) as ei:
             hs.hsgen_reduce_generalized(g.ctx, n_g, Hd.data_ptr(), Sd.data_ptr(), n_g, 0)
         assert ei.value.status == hs.ENUMERIC
+        # the failing leading minor is reported: inside the shifted block (N_G 700) or the first row
+        minor = int(re.search(r"leading minor (\d+)", str(ei.value)).group(1))
+        assert (600 < minor <= n_g) if n_g > 600 else minor == 1, minor
         # the context stays usable
         sysm2, H2, S2 = pd_problem(seed=6, n_g=64)
         Hd2, Sd2 = to_device(H2, "U"), to_device(S2, "U")

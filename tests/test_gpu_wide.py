@@ -1,0 +1,178 @@
+"""GPU parity beyond the small cases, through the C ABI:
+
+* the caller-supplied Wronskian W_l (App. A.1): equal to the computed
+  u_dot u' - u u_dot' it must leave H and S bit for bit unchanged; scaled by
+  c_l it must match the oracle given the same W_l;
+* the FP64 form at 64 atoms / N_G 12000 (sampled entries) and at the
+  benchmark workload, 256 atoms / N_G 20000 (whole columns);
+* the split form at the benchmark workload on whole columns: every row of
+  ten columns placed on tile, band and tile-group edges and the last column
+  (the ragged tail), so every 256-row block of the triangle is checked.
+
+Tolerances as in the other parity tests: relative Frobenius <= 1e-12 (FP64
+form) or <= 1e-11 (split form) over the compared entries, and per entry
+|dH_ij| <= 1e-10 ||w_i|| ||x_j|| (S: ||y_j||).
+"""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import make_config, make_system, kpoint_list
+
+from _parity import compare, normwise_scales, tri_mask
+
+pytestmark = pytest.mark.gpu
+
+PER_ENTRY = 1e-10
+REL = {"fp64": 1e-12, "split": 1e-11}
+# columns of the 20000 x 20000 triangle: tile (64 / 128 columns) and band
+# (1024 columns) edges, an interior column, and the last one
+COLS4 = [0, 63, 64, 127, 1023, 1024, 10111, 16384, 19455, 19999]
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1602_06589_gb300 import hsgen
+
+    assert torch.cuda.is_available()
+    return hsgen
+
+
+def mixed_system(seed=43):
+    lat = np.array([[10.0, 0.3, 0.0], [0.0, 11.0, 0.2], [0.1, 0.0, 9.5]])
+    return make_system(seed, lat, [(3, 1.5), (5, 1.6), (1, 1.7)], [2, 2, 1])
+
+
+def build(hs, sysm, kv, form, **kw):
+    import torch
+
+    prec = hs.SPLIT if form == "split" else hs.FP64
+    with hs.Generator(sysm, precision=prec, **kw) as g:
+        H, S = g.build(torch.from_numpy(kv).cuda())
+        torch.cuda.synchronize()
+        return H.cpu().numpy(), S.cpu().numpy()
+
+
+@pytest.mark.parametrize("form", ["fp64", "split"])
+def test_wronskian_equal_to_computed_is_bitwise(hs, form):
+    sysm = mixed_system()
+    kv = kpoint_list(sysm.lattice, (0.12, -0.31, 0.07), 300)
+    H0, S0 = build(hs, sysm, kv, form)
+    given = copy.deepcopy(sysm)
+    for ty in given.types:
+        ty.wronskian = ty.udot * ty.du - ty.u * ty.dudot
+    H1, S1 = build(hs, given, kv, form)
+    assert np.array_equal(H0, H1) and np.array_equal(S0, S1)
+
+
+@pytest.mark.parametrize("form", ["fp64", "split"])
+def test_wronskian_scaled_vs_oracle(hs, form):
+    sysm = mixed_system(seed=47)
+    rng = np.random.default_rng(11)
+    for ty in sysm.types:
+        ty.wronskian = rng.uniform(0.5, 2.0, ty.lmax + 1) * (ty.udot * ty.du - ty.u * ty.dudot)
+    kv = kpoint_list(sysm.lattice, (0.05, 0.21, -0.13), 260)
+    H, S = build(hs, sysm, kv, form)
+    Ho, So = oracle.build_HS(sysm, kv)
+    wn, xn, yn = normwise_scales(sysm, kv)
+    m = tri_mask(kv.shape[0])
+    for A, B, sc in ((H, Ho, xn), (S, So, yn)):
+        rf, pe = compare(A, B, wn, sc, m)
+        assert rf <= REL[form] and pe <= PER_ENTRY, (rf, pe)
+    # and the scaling is really used: the result differs from the computed W_l's
+    plain = copy.deepcopy(sysm)
+    for ty in plain.types:
+        ty.wronskian = None
+    Hp, _ = oracle.build_HS(plain, kv)
+    assert np.linalg.norm((Hp - Ho)[m]) > 1e-3 * np.linalg.norm(Ho[m])
+
+
+def test_fp64_config2_sampled(hs):
+    """64 atoms / 4 species, l_max 10, N_G 12000 in the FP64 form."""
+    import torch
+
+    w = make_config(2)
+    kv = w.kvecs[0]
+    with hs.Generator(w.system, precision=hs.FP64) as g:
+        H, S = g.build(torch.from_numpy(kv).cuda())
+        torch.cuda.synchronize()
+        n = kv.shape[0]
+        rng = np.random.default_rng(2)
+        idx = np.unique(np.r_[0, np.sort(rng.choice(n, 14, replace=False)), n - 1])
+        r, c = np.meshgrid(idx, idx, indexing="ij")
+        sel = r <= c
+        ti = torch.from_numpy(r[sel]).cuda(), torch.from_numpy(c[sel]).cuda()
+        Hg, Sg = H[ti].cpu().numpy(), S[ti].cpu().numpy()
+    Ho, So = oracle.HS_entries(w.system, kv, r[sel], c[sel])
+    assert np.linalg.norm(Hg - Ho) <= REL["fp64"] * np.linalg.norm(Ho)
+    assert np.linalg.norm(Sg - So) <= REL["fp64"] * np.linalg.norm(So)
+
+
+@pytest.fixture(scope="module")
+def config4_columns():
+    """The oracle's whole columns COLS4 of H and S at 256 atoms / N_G 20000."""
+    w = make_config(4)
+    Ho, So, norms = oracle.HS_columns(w.system, w.kvecs[0], COLS4, norms=True)
+    return w, Ho, So, norms
+
+
+def check_columns(Hc, Sc, Ho, So, norms, rel):
+    """Hc, Sc: the library's columns COLS4 (every row). Upper triangle: rows
+    0..j of column j are compared, the rows below must be untouched (zero)."""
+    wn, xn, yn = norms
+    n = Hc.shape[0]
+    out = {}
+    for name, A, B, sc in (("H", Hc, Ho, xn), ("S", Sc, So, yn)):
+        d2 = b2 = 0.0
+        per = 0.0
+        for k, j in enumerate(COLS4):
+            a, b = A[: j + 1, k], B[: j + 1, k]
+            d2 += float(np.sum(np.abs(a - b) ** 2))
+            b2 += float(np.sum(np.abs(b) ** 2))
+            per = max(per, float(np.max(np.abs(a - b) / (wn[: j + 1] * sc[k]))))
+            assert np.all(A[j + 1:, k] == 0), f"{name}: column {j} written below the diagonal"
+            assert A[j, k].imag == 0.0
+        out[name] = (np.sqrt(d2 / b2), per)
+        assert out[name][0] <= rel and per <= PER_ENTRY, (name, out[name])
+    return out
+
+
+def library_columns(hs, w, form, **kw):
+    import torch
+
+    prec = hs.SPLIT if form == "split" else hs.FP64
+    kv = torch.from_numpy(w.kvecs[0]).cuda()
+    with hs.Generator(w.system, precision=prec, **kw) as g:
+        if form == "split":
+            H, S = g.autotune(kv)  # the benchmark's launch configuration
+        else:
+            H, S = g.build(kv)
+        torch.cuda.synchronize()
+        ci = torch.tensor(COLS4, device="cuda")
+        Hc, Sc = H[:, ci].cpu().numpy(), S[:, ci].cpu().numpy()
+        del H, S
+    return Hc, Sc
+
+
+@pytest.mark.slow
+def test_split_config4_columns(hs, config4_columns):
+    """256 atoms, l_max 10, N_G 20000, split form as the benchmark runs it."""
+    w, Ho, So, norms = config4_columns
+    Hc, Sc = library_columns(hs, w, "split")
+    check_columns(Hc, Sc, Ho, So, norms, REL["split"])
+
+
+@pytest.mark.slow
+def test_fp64_config4_columns(hs, config4_columns):
+    """The same workload in the FP64 form (depth 63 488 rows: W and X of
+    about 20 GB each, byte offsets far beyond 2^32)."""
+    w, Ho, So, norms = config4_columns
+    Hc, Sc = library_columns(hs, w, "fp64")
+    check_columns(Hc, Sc, Ho, So, norms, REL["fp64"])
