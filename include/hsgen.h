@@ -69,6 +69,16 @@ typedef enum {
 
 enum { HSGEN_FP64 = 0, HSGEN_SPLIT = 1 };
 enum { HSGEN_S_CONTRACTION = 0, HSGEN_S_LEGENDRE = 1 };
+/* How the split form cuts an FP64 product into BF16 tensor-core products (no
+ * counterpart in the paper, which is all FP64):
+ *  HSGEN_SCHEME_SLICES: s slices per operand, s(s+1)/2 products (Ozaki
+ *    scheme I);
+ *  HSGEN_SCHEME_MODULI: operands rounded to b-bit integers, one product per
+ *    modulus, exact integer result by the Chinese remainder theorem (Ozaki
+ *    scheme II), 10..14 moduli;
+ *  HSGEN_SCHEME_AUTO: moduli when a count of at most 14 meets target_rel_err
+ *    (and no slice count is forced), otherwise slices. */
+enum { HSGEN_SCHEME_AUTO = 0, HSGEN_SCHEME_SLICES = 1, HSGEN_SCHEME_MODULI = 2 };
 
 typedef struct {
   int precision;            /* HSGEN_FP64 (default) or HSGEN_SPLIT                  */
@@ -84,6 +94,9 @@ typedef struct {
                             /* the m-summed form of Sec. 3.1 (Eq. overlap_no_m) in */
                             /* FP64, used when all K_t lie on one lattice k + G,   */
                             /* otherwise the contraction (see hsgen_stats.s_form)  */
+  int scheme;               /* split form: HSGEN_SCHEME_* (default AUTO)            */
+  int moduli;               /* split form, moduli scheme: 10..14, 0 = from the      */
+                            /* target and the depth                                 */
 } hsgen_options;
 
 /* Radial data of one atom species (App. A.1 and A.2). All arrays are host
@@ -135,6 +148,12 @@ typedef struct {
                            /* the device staging of H, S, before the build      */
   double ms_download;      /* host outputs: copy-out time after the build ends  */
                            /* (the part not overlapped with the last tiles)     */
+  int scheme;              /* split form of the last pass: HSGEN_SCHEME_SLICES  */
+                           /* or HSGEN_SCHEME_MODULI                            */
+  int moduli;              /* moduli used (moduli scheme)                       */
+  int bits;                /* integer bits per operand (moduli scheme)          */
+  int products;            /* BF16 products per FP64 product of the contraction */
+  int atom_chunks;         /* passes over the atoms (a6) of the last build      */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */

@@ -112,7 +112,7 @@ static void free_system(hsgen_ctx *ctx) {
 // Chunks of atoms [a0, a1) processed per pass over the depth (a6).
 static std::vector<std::pair<int, int>> atom_chunks(const hsgen_ctx *ctx) {
   int na = (int)ctx->toa.size();
-  int c = ctx->opt.atom_chunk > 0 ? ctx->opt.atom_chunk : na;
+  int c = ctx->opt.atom_chunk > 0 ? ctx->opt.atom_chunk : (ctx->auto_chunk > 0 ? ctx->auto_chunk : na);
   std::vector<std::pair<int, int>> out;
   for (int a = 0; a < na; a += c) out.push_back({a, std::min(na, a + c)});
   return out;
@@ -135,6 +135,8 @@ hsgen_status hsgen_default_options(hsgen_options *opt) {
   opt->atom_chunk = 0;
   opt->wait_timeout_ns = 2000000000LL;
   opt->s_form = HSGEN_S_CONTRACTION;
+  opt->scheme = HSGEN_SCHEME_AUTO;
+  opt->moduli = 0;
   return HSGEN_OK;
 }
 
@@ -149,6 +151,9 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   if (o.atom_chunk < 0 || o.slices < 0 || o.slices > kMaxSlices) return HSGEN_EINVAL;
   if (!(o.target_rel_err > 0.0) || o.wait_timeout_ns <= 0) return HSGEN_EINVAL;
   if (o.s_form != HSGEN_S_CONTRACTION && o.s_form != HSGEN_S_LEGENDRE) return HSGEN_EINVAL;
+  if (o.scheme != HSGEN_SCHEME_AUTO && o.scheme != HSGEN_SCHEME_SLICES && o.scheme != HSGEN_SCHEME_MODULI)
+    return HSGEN_EINVAL;
+  if (o.moduli != 0 && (o.moduli < kMinModuli || o.moduli > 14)) return HSGEN_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -163,7 +168,8 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   ctx->device = cuda_device;
   ctx->opt = o;
   if (const char *ks = std::getenv("HSGEN_KSEG_BLOCKS")) ctx->kseg_blocks = std::max(1, std::atoi(ks));
-  if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess) {
+  if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess ||
+      split_upload_tables() != cudaSuccess) {
     delete ctx;
     return HSGEN_ECUDA;
   }
@@ -418,7 +424,8 @@ static WsLayout ws_layout(const hsgen_ctx *ctx, int n_g, int chunk_depth, bool s
   L.F = take(sizeof(double2) * (size_t)ctx->types.size() * n_g * kRadStride);
   L.W = take(sizeof(double2) * (size_t)chunk_depth * n_g);
   L.X = take(sizeof(double2) * (size_t)chunk_depth * n_g);
-  L.split = split ? take(split_workspace_bytes(n_g, chunk_depth, slices)) : o;
+  (void)slices;
+  L.split = split ? take(split_workspace_bytes(ctx, n_g, chunk_depth)) : o;
   L.total = o;
   return L;
 }
@@ -589,6 +596,18 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   if (hdev != sdev) return set_err(ctx, HSGEN_EINVAL, "build_HS: H and S must both be device or both host");
   bool split = ctx->opt.precision == HSGEN_SPLIT;
   int slices = split ? choose_slices(ctx->opt.target_rel_err, ctx->opt.slices) : 0;
+  // a6: without a caller's atom_chunk the split form takes as many atoms per
+  // pass as keep its workspace within the budget (HSGEN_WS_BYTES, default 176e9)
+  ctx->auto_chunk = 0;
+  if (split && ctx->opt.atom_chunk <= 0) {
+    double budget = 176e9;
+    if (const char *e = std::getenv("HSGEN_WS_BYTES")) budget = std::max(1e6, std::atof(e));
+    const int na = (int)ctx->toa.size();
+    for (int parts = 1; parts <= na; ++parts) {
+      ctx->auto_chunk = (parts == 1) ? 0 : (na + parts - 1) / parts;
+      if ((double)ws_layout(ctx, n_g, max_chunk_depth(ctx), split, slices).total <= budget) break;
+    }
+  }
   WsLayout L = ws_layout(ctx, n_g, max_chunk_depth(ctx), split, slices);
   hsgen_status st = ensure_ws(ctx, ctx->ws_main, L.total);
   if (st != HSGEN_OK) return st;
@@ -677,6 +696,16 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   ctx->stats.precision = ctx->opt.precision;
   ctx->stats.n_kpoints = 1;
   ctx->stats.flops_algorithmic = algorithmic_flops(ctx, n_g);
+  ctx->stats.atom_chunks = (int)atom_chunks(ctx).size();
+  if (split) {
+    const SplitPlan &pl = ctx->last_plan;
+    ctx->stats.scheme = pl.scheme == kSchemeModuli ? HSGEN_SCHEME_MODULI : HSGEN_SCHEME_SLICES;
+    ctx->stats.moduli = pl.nmod;
+    ctx->stats.bits = pl.bits;
+    ctx->stats.products = pl.scheme == kSchemeModuli ? pl.nmod : pl.slices * (pl.slices + 1) / 2;
+  } else {
+    ctx->stats.scheme = ctx->stats.moduli = ctx->stats.bits = ctx->stats.products = 0;
+  }
   ctx->stats.kernel_launches = ctx->launches;
   ctx->stats.s_form = job.leg ? HSGEN_S_LEGENDRE : HSGEN_S_CONTRACTION;
   ctx->phase_used[0] = atom_chunks(ctx).size() == 1;

@@ -55,6 +55,16 @@ struct Workspace {
   size_t bytes = 0;
 };
 
+// Split form of one pass: slices (Ozaki scheme I: s(s+1)/2 BF16 products per
+// FP64 product) or moduli (Ozaki scheme II: one BF16 product per modulus on
+// b-bit integer operands). `slices` is also the slice count of T and of
+// X = T W in either form.
+enum { kSchemeSlices = 1, kSchemeModuli = 2 };
+struct SplitPlan {
+  int scheme = kSchemeSlices;
+  int slices = 0, nmod = 0, bits = 0;
+};
+
 }  // namespace hsg
 
 struct hsgen_ctx {
@@ -95,6 +105,9 @@ struct hsgen_ctx {
   int kseg_blocks = 128;            // split form: k-blocks (64 deep) per H/S launch
   int tile_band = 16;               // split form: column blocks per band of the tile order
   int tiles_band = 0;               // band the cached tile list was built with
+  int tiles_bn = 0;                 // tile width (complex columns) of that list
+  hsg::SplitPlan last_plan;         // split form of the last pass
+  int auto_chunk = 0;               // atoms per pass chosen by the library (0: all), see atom_chunk
   std::vector<int2> tiles_host;     // host copy of that list (column bands of the overlapped copies)
   cudaStream_t copy_stream = nullptr;  // host outputs: copies of finished column bands
   cudaEvent_t copy_ev = nullptr;       // orders each copy after the launch that finished its bands

@@ -110,6 +110,24 @@ struct GemmProblem {
   int a_shift_planes;       // batch mode: A planes per depth shift (the shifted copies of T)
   const int2 *tile_list;    // triangle mode: (row block, column block) of every tile, L2-friendly order
   long long tile_begin;     // first global tile index of this problem
+  // moduli form: per-tile residue store (one byte per output and modulus),
+  // the problem's first slot in it, and whether this launch starts / ends the depth
+  unsigned char *res;
+  long long res_base;
+  int seg_first, seg_last;
+};
+
+// Moduli form (Ozaki scheme II): pairwise coprime moduli m_i <= 256, CRT
+// weights c_i = (M / m_i) ((M / m_i)^-1 mod m_i) mod M as 128-bit integers
+// (lo, hi), M = prod m_i, and 2^64 / M for the quotient estimate.
+constexpr int kMaxModuli = 14;
+struct CrtConsts {
+  int n;
+  int m[kMaxModuli];
+  float inv_m[kMaxModuli];
+  unsigned long long c_lo[kMaxModuli], c_hi[kMaxModuli];
+  unsigned long long M_lo, M_hi, Mh_lo, Mh_hi;  // M and M / 2
+  float q_scale;
 };
 
 struct GemmParams {
@@ -125,6 +143,7 @@ struct GemmParams {
   int s;
   int *status;
   unsigned long long timeout_ns;
+  CrtConsts crt;  // moduli form only
 };
 
 // ---------------------------------------------------------------------------
@@ -226,6 +245,14 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
 
@@ -686,6 +713,354 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// The moduli form (Ozaki scheme II) of the H/S contraction
+// ---------------------------------------------------------------------------
+// Every operand column is integerised once, N = round(v 2^(b - e)) with one
+// power-of-two scale per column (|N| <= 2^b), and stored as its balanced
+// residues r_i = N mod m_i (|r_i| <= 128, exact in BF16) for n pairwise
+// coprime moduli m_i <= 256. The integer product C' = P'^H Q' is then known
+// from its residues C' mod m_i = (sum_k r_i(P) r_i(Q)) mod m_i: one BF16
+// product per modulus instead of s(s+1)/2 slice pairs. b is the largest value
+// with 4 K 2^(2b) < M = prod m_i (K = complex depth), so the balanced
+// representative of C' in [-M/2, M/2) is C' itself (Chinese remainder
+// theorem); only the rounding of P and Q to b-bit integers is an error.
+//
+// Tiles are 256 output rows x 128 complex columns (CTA pair, M = 256): every
+// MMA is N = 256, the B operand [Qr | Qi] (r half) or [Qi | -Qr] (i half)
+// split by rows between the two CTAs. Per modulus the depth runs in chunks
+// of 1024 products (exact in FP32) into one of two TMEM accumulators; the
+// epilogue adds each chunk into int32 sums in registers, reduces them mod m_i
+// at the end of the modulus and keeps the residue bytes in a per-tile store
+// in global memory, added mod m_i across depth segments (separate launches).
+// The launch that ends the depth reconstructs C' from the residues (128-bit
+// integers), scales it to FP64 and writes (or adds) the tile of H or S.
+constexpr int BNC = 128;  // complex output columns of a moduli-form tile
+constexpr int CKB = 8;    // 64-deep k-blocks per accumulation chunk (x 2 halves = 1024 products)
+
+__device__ __forceinline__ Tile decode_tile_crt(const GemmParams &P, long long t, long long &slot) {
+  int pi = 0, hi = P.nprob;
+  while (hi - pi > 1) {
+    const int mid = (pi + hi) >> 1;
+    if (problem(P, mid).tile_begin <= t) pi = mid; else hi = mid;
+  }
+  const GemmProblem &pr = problem(P, pi);
+  const long long lt = t - pr.tile_begin;
+  const int2 bij = pr.tile_list[lt];
+  Tile ti;
+  ti.prob = pi;
+  ti.m0 = bij.x * BMT;
+  ti.n0 = bij.y * BNC;
+  ti.b_k0 = 0;
+  ti.a_p0 = 0;
+  ti.c_row0 = 0;
+  ti.nkb = (pr.K + BK - 1) / BK;
+  slot = pr.res_base + lt;
+  return ti;
+}
+
+__device__ __forceinline__ void ld_v4(const uint4 *p, uint32_t (&w)[4]) {
+  asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st_v4(uint4 *p, const uint32_t (&w)[4]) {
+  asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+
+// a mod m for 0 <= a < 2^31, 2 <= m <= 256: the float quotient is within 3
+// of the true one (rounding of a, of 1/m and of the product), then corrected
+__device__ __forceinline__ int mod_small(int a, int m, float inv_m) {
+  const int q = __float2int_rz(__int2float_rz(a) * inv_m);
+  int r = a - q * m;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r = (r < 0) ? r + m : r;
+    r = (r >= m) ? r - m : r;
+  }
+  return r;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    crt_gemm_kernel(const __grid_constant__ GemmParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES);
+  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NST + 2 * NACC + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NST, accf0 = empty0 + 8 * NST,
+                 acce0 = accf0 + 8 * NACC, tdown = acce0 + 8 * NACC;
+  const uint32_t sbase = smem_u32(smem);
+  const unsigned long long tmo = P.timeout_ns;
+  const uint32_t rank = cta_rank();
+  const bool leader = rank == 0;
+  const uint32_t lead_full0 = map_rank(full0, 0), lead_acce0 = map_rank(acce0, 0);
+  const long long pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int NM = P.crt.n;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < NACC; ++i) {
+      mbar_init(accf0 + 8 * i, 1);
+      mbar_init(acce0 + 8 * i, 16);
+    }
+    mbar_init(tdown, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == WARP_MMA) {
+    tc_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tbase = *tmem_slot;
+  const unsigned long long drain = tmo > 1000000000ull ? tmo : 1000000000ull;
+  if (warp == WARP_TMA) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_AUX));
+    // ------------------------------ TMA producer ------------------------------
+    uint32_t it = 0;
+    bool ok = true;
+    for (long long t = pair; t < P.ntiles && ok; t += npairs) {
+      long long slot;
+      const Tile ti = decode_tile_crt(P, t, slot);
+      const GemmProblem &pr = problem(P, ti.prob);
+      const CUtensorMap *mA = map_a(P, ti.prob), *mB = map_b(P, ti.prob);
+      for (int i = 0; i < NM && ok; ++i)
+        for (int kb = 0; kb < ti.nkb && ok; kb += KPS) {
+          const int nk = min(KPS, ti.nkb - kb);
+          const uint32_t bytes = nk * 2 * (A_BYTES + B_BYTES);
+          for (int h = 0; h < 2; ++h, ++it) {
+            const int st = it % NST;
+            const uint32_t round = it / NST;
+            if (!warp_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
+              if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
+              ok = false;
+              break;
+            }
+            const uint32_t sA0 = sbase + st * STAGE_BYTES;
+            const uint32_t mbar = lead_full0 + 8 * st;
+            const int pa = i * pr.a_pps + h;
+            // B rows [0, 128) in CTA 0, [128, 256) in CTA 1: [re | im] (h = 0), [im | -re] (h = 1)
+            const int pb = i * pr.b_pps + h + (int)rank;
+            const int kbA = pr.kb_begin + kb;
+            if (elect_one()) {
+              if (leader) mbar_expect_tx(full0 + 8 * st, bytes);
+              for (int j = 0; j < nk; ++j) {
+                tma_load_3d(sA0 + j * A_BYTES, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA + j);
+                tma_load_3d(sA0 + STAGE_A + j * B_BYTES, mB, mbar, 0, ti.n0, pb * pr.b_nkb + kbA + j);
+              }
+            }
+            __syncwarp();
+          }
+        }
+    }
+    for (int st = 0; st < NST && leader; ++st) {
+      if (it <= (uint32_t)st) break;
+      const uint32_t j = st + NST * ((it - 1 - st) / NST);
+      if (!warp_wait(full0 + 8 * st, (j / NST) & 1, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
+    }
+  } else if (warp == WARP_MMA) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_AUX));
+    if (leader) {
+      // ------------------------------ MMA issuer --------------------------------
+      const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + STAGE_A);
+      uint32_t it = 0, cc = 0;
+      bool ok = true;
+      for (long long t = pair; t < P.ntiles && ok; t += npairs) {
+        long long slot;
+        const Tile ti = decode_tile_crt(P, t, slot);
+        for (int i = 0; i < NM && ok; ++i)
+          for (int kc0 = 0; kc0 < ti.nkb && ok; kc0 += CKB, ++cc) {
+            const int kc1 = min(ti.nkb, kc0 + CKB);
+            const int buf = cc % NACC;
+            const uint32_t use = cc / NACC;
+            if (!warp_wait<true>(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
+              if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dacc = tbase + buf * 256;
+            uint32_t accum = 0;
+            for (int kb = kc0; kb < kc1 && ok; kb += KPS) {
+              const int nk = min(KPS, kc1 - kb);
+              for (int h = 0; h < 2; ++h, ++it) {
+                const int st = it % NST;
+                if (!warp_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
+                  if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint64_t da = descA0 + (uint64_t)(st * (STAGE_BYTES >> 4));
+                const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4));
+                if (elect_one()) {
+                  for (int j = 0; j < nk; ++j) {
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                      tc_mma(dacc, da + (uint64_t)(j * (A_BYTES >> 4)) + 2 * kk,
+                             db + (uint64_t)(j * (B_BYTES >> 4)) + 2 * kk, IDESC_N256, (accum | j | kk) ? 1u : 0u);
+                  }
+                  tc_commit(empty0 + 8 * st);
+                }
+                __syncwarp();
+                accum = 1;
+              }
+            }
+            if (ok) {
+              if (elect_one()) tc_commit(accf0 + 8 * buf);
+              __syncwarp();
+            }
+          }
+      }
+      if (elect_one()) tc_commit(tdown);
+      __syncwarp();
+      if (!warp_wait(tdown, 0, drain) && lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
+    }
+  } else if (warp < WARP_TMA) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_EPI));
+    // ------------------------------ epilogue ----------------------------------
+    // Warp w: TMEM lane quadrant w % 4 (rows), accumulator half hf = w / 4
+    // (hf 0: real parts, hf 1: imaginary parts of the tile's 128 columns);
+    // each thread holds the int32 sums of its row's 128 values.
+    const int qd = warp & 3;
+    const int hf = warp >> 2;
+    const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
+    uint32_t cc = 0;
+    bool ok = true;
+    for (long long t = pair; t < P.ntiles && ok; t += npairs) {
+      long long slot;
+      const Tile ti = decode_tile_crt(P, t, slot);
+      const GemmProblem &pr = problem(P, ti.prob);
+      const int nkc = (ti.nkb + CKB - 1) / CKB;
+      // this thread's 128 residue bytes of modulus i
+      auto res_ptr = [&](int i) {
+        return (uint4 *)(pr.res + ((((size_t)slot * NM + i) * 2 + rank) * 256 + threadIdx.x) * 128);
+      };
+      for (int i = 0; i < NM && ok; ++i) {
+        int acc[128];
+#pragma unroll
+        for (int u = 0; u < 128; ++u) acc[u] = 0;
+        for (int kc = 0; kc < nkc && ok; ++kc, ++cc) {
+          const int buf = cc % NACC;
+          const uint32_t use = cc / NACC;
+          int got = 0;
+          if (lane == 0) got = mbar_wait(accf0 + 8 * buf, use & 1, tmo) ? 1 : 0;
+          got = __shfl_sync(0xffffffffu, got, 0);
+          if (!got) {
+            if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_EPILOGUE);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t tacc = tbase + lane_off + buf * 256 + hf * 128;
+          uint32_t v[16];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            tc_ld16(tacc + q * 16, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[q * 16 + u] += __float2int_rn(__uint_as_float(v[u]));
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(lead_acce0 + 8 * buf);
+        }
+        if (!ok) break;
+        // end of modulus i in this launch: sums mod m_i, added to the residues
+        // of the earlier depth segments
+        const int m = P.crt.m[i];
+        const float inv = P.crt.inv_m[i];
+        const int off = m << 22;  // makes every sum non-negative (|sum| <= 32 chunks x 2^24)
+#pragma unroll
+        for (int u = 0; u < 128; ++u) acc[u] = mod_small(acc[u] + off, m, inv);
+        uint4 *rp = res_ptr(i);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          // ordered loads and stores: one 16-byte group of residues in flight at a time
+          uint32_t w[4] = {0u, 0u, 0u, 0u};
+          if (!pr.seg_first) ld_v4(rp + g, w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint32_t outw = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              int r = acc[g * 16 + q * 4 + b] + (int)((w[q] >> (8 * b)) & 0xFFu);
+              r = (r >= m) ? r - m : r;
+              outw |= (uint32_t)r << (8 * b);
+            }
+            w[q] = outw;
+          }
+          st_v4(rp + g, w);
+        }
+      }
+      if (!ok) break;
+      if (!pr.seg_last) continue;
+      // ---- last segment: C' from its residues (CRT), scaled to FP64 by 2^(eA + eB - 2b)
+      const int row = ti.m0 + (int)rank * BM + qd * 32 + lane;
+      if (row >= pr.M) continue;
+      const int eA = pr.expA[row];
+      double *Cd = (double *)pr.C + 2 * (long long)row + hf;
+      const unsigned __int128 Mv = ((unsigned __int128)P.crt.M_hi << 64) | P.crt.M_lo;
+      const unsigned __int128 Mh = ((unsigned __int128)P.crt.Mh_hi << 64) | P.crt.Mh_lo;
+      for (int g = 0; g < 8; ++g) {
+        uint4 rv[kMaxModuli];
+#pragma unroll
+        for (int i = 0; i < kMaxModuli; ++i)
+          if (i < NM) rv[i] = res_ptr(i)[g];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int u = g * 16 + q * 4 + b;
+            const int col = ti.n0 + u;
+            const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
+            if (!keep) continue;
+            unsigned __int128 sum = 0;
+#pragma unroll
+            for (int i = 0; i < kMaxModuli; ++i) {
+              if (i >= NM) break;
+              const uint32_t word = (q == 0) ? rv[i].x : (q == 1) ? rv[i].y : (q == 2) ? rv[i].z : rv[i].w;
+              const unsigned long long r = (word >> (8 * b)) & 0xFFu;
+              sum += (unsigned __int128)(r * P.crt.c_lo[i]) + ((unsigned __int128)__umul64hi(r, P.crt.c_lo[i]) << 64) +
+                     ((unsigned __int128)(r * P.crt.c_hi[i]) << 64);
+            }
+            // sum mod M: quotient estimated from the high word, then corrected
+            const float qf = (float)(unsigned long long)(sum >> 64) * P.crt.q_scale - 0.5f;
+            const unsigned long long q0 = qf > 0.f ? (unsigned long long)qf : 0ull;
+            sum -= (unsigned __int128)q0 * Mv;
+            if (sum >= Mv) sum -= Mv;
+            const bool neg = sum > Mh;
+            const unsigned __int128 mag = neg ? Mv - sum : sum;
+            double x = fma((double)(unsigned long long)(mag >> 64), 18446744073709551616.0,
+                           (double)(unsigned long long)mag);
+            const int e = eA + pr.expB[col] - pr.F;
+            const double scl =
+                (e > -1022 && e < 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+            x = (neg ? -x : x) * scl;
+            double *dst = Cd + 2 * (size_t)col * pr.ldc;
+            if (pr.accumulate) x += *dst;
+            if (hf == 1 && pr.uplo && row == col) x = 0.0;
+            *dst = x;
+          }
+      }
+    }
+  } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_AUX));
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  if (warp == WARP_MMA) tc_dealloc(tbase, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
 // Slicing kernel: one CTA per column.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ long long to_fixed(double v, int shift) {
@@ -762,6 +1137,82 @@ __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ 
       base[0] = __float2bfloat16_rn((float)dr);
       base[plane_stride] = __float2bfloat16_rn((float)di);
       if (planes == 3) base[2 * plane_stride] = __float2bfloat16_rn((float)-dr);
+    }
+  }
+}
+
+// Moduli form: residues of the b-bit integers N = round(v 2^(b - e)) (one
+// scale 2^e per column) for every modulus, balanced to |r| <= 128, as BF16
+// planes in the k-blocked layout of slice_kernel; plane i * planes + {0, 1, 2}
+// holds re, im, -re of modulus i. N mod m is formed from N's base-256 digits
+// and the table 256^j mod m, so no 64-bit division is needed.
+__constant__ int c_pow256[kMaxModuli][6];
+
+__global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict__ src, long long lds, int K,
+                                                      const double *__restrict__ urow, int b, CrtConsts crt,
+                                                      int planes, __nv_bfloat16 *__restrict__ dst, long long ldk,
+                                                      int ncols, long long plane_stride, int *__restrict__ expo) {
+  const int col = blockIdx.x;
+  const double2 *c = src + (size_t)col * lds;
+  __shared__ double red[8];
+  __shared__ int e_sh;
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double2 v = c[k];
+    const double u = urow ? urow[k] : 1.0;
+    mx = fmax(mx, fmax(fabs(v.x * u), fabs(v.y * u)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    const int e = (m > 0.0) ? ilogb(m) + 1 : 0;
+    e_sh = e;
+    expo[col] = e;
+  }
+  __syncthreads();
+  const int shift = b - e_sh;
+  for (int k = threadIdx.x; k < (int)ldk; k += blockDim.x) {
+    __nv_bfloat16 *out = dst + ((size_t)(k >> 6) * ncols + col) * 64 + (k & 63);
+    long long N[2] = {0, 0};
+    if (k < K) {
+      double2 v = c[k];
+      if (urow) {
+        const double u = urow[k];
+        v.x *= u;
+        v.y *= u;
+      }
+      N[0] = to_fixed(v.x, shift);
+      N[1] = to_fixed(v.y, shift);
+    }
+    int dg[2][6];
+    bool ng[2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+      ng[z] = N[z] < 0;
+      const unsigned long long a = ng[z] ? (unsigned long long)(-N[z]) : (unsigned long long)N[z];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) dg[z][j] = (int)((a >> (8 * j)) & 0xFFu);
+    }
+    for (int i = 0; i < crt.n; ++i) {
+      const int m = crt.m[i];
+      int r[2];
+#pragma unroll
+      for (int z = 0; z < 2; ++z) {
+        int acc = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += dg[z][j] * c_pow256[i][j];
+        int x = mod_small(acc, m, crt.inv_m[i]);  // |N| mod m
+        if (ng[z] && x) x = m - x;                // N mod m
+        r[z] = (2 * x > m) ? x - m : x;           // balanced: |r| <= m / 2 <= 128
+      }
+      __nv_bfloat16 *base = out + (size_t)i * planes * plane_stride;
+      base[0] = __float2bfloat16_rn((float)r[0]);
+      base[plane_stride] = __float2bfloat16_rn((float)r[1]);
+      if (planes == 3) base[2 * plane_stride] = __float2bfloat16_rn((float)-r[0]);
     }
   }
 }
@@ -852,6 +1303,105 @@ cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_crt(GemmParams &P, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(crt_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (P.ntiles <= 0) return cudaSuccess;
+  const long long pairs = std::min<long long>(P.ntiles, max_pairs());
+  crt_gemm_kernel<<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residue(const double2 *src, long long lds, int K, const double *urow, int b, const CrtConsts &crt,
+                           int planes, __nv_bfloat16 *dst, long long ldk, long long plane_stride, int *expo,
+                           int ncols, cudaStream_t st) {
+  if (ncols <= 0) return cudaSuccess;
+  residue_kernel<<<ncols, 256, 0, st>>>(src, lds, K, urow, b, crt, planes, dst, ldk, ncols, plane_stride, expo);
+  return cudaGetLastError();
+}
+
+// ---- moduli form: constants --------------------------------------------------
+// pairwise coprime moduli <= 256 (2^8, 3.5.17, 11.23, 251, 13.19, then primes
+// and 7.31), largest first: n of them give M = prod m_i of about 7.9 n bits
+constexpr int kModuli[kMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199};
+// error model of the moduli form (relative Frobenius error of H and S for
+// b-bit operands): about kCrtErr 2^-b
+constexpr double kCrtErr = 32.0;
+
+unsigned __int128 crt_M(int n) {
+  unsigned __int128 M = 1;
+  for (int i = 0; i < n; ++i) M *= (unsigned)kModuli[i];
+  return M;
+}
+
+// The largest b with 4 K 2^(2b) < M (K: complex depth), at most 47: then
+// |C'| <= 2 K 2^(2b) < M / 2 for b-bit operands, so C' is recovered exactly.
+int crt_bits(int n, long long K) {
+  const unsigned __int128 M = crt_M(n);
+  const unsigned __int128 k4 = (unsigned __int128)(4 * std::max(K, 1LL));
+  int b = 0;
+  while (b < 47) {
+    const int sh = 2 * (b + 1);
+    if (sh > 120 || (k4 << sh) >> sh != k4 || (k4 << sh) >= M) break;
+    ++b;
+  }
+  return b;
+}
+
+int inv_mod(int a, int m) {  // a^-1 mod m (gcd(a, m) = 1)
+  int t = 0, nt = 1, r = m, nr = a % m;
+  while (nr) {
+    const int q = r / nr;
+    int x = t - q * nt;
+    t = nt;
+    nt = x;
+    x = r - q * nr;
+    r = nr;
+    nr = x;
+  }
+  return t < 0 ? t + m : t;
+}
+
+CrtConsts make_crt(int n) {
+  CrtConsts c;
+  std::memset(&c, 0, sizeof(c));
+  c.n = n;
+  const unsigned __int128 M = crt_M(n);
+  for (int i = 0; i < n; ++i) {
+    const int m = kModuli[i];
+    const unsigned __int128 Mi = M / (unsigned)m;
+    const int y = inv_mod((int)(Mi % (unsigned)m), m);
+    const unsigned __int128 ci = (Mi * (unsigned)y) % M;
+    c.m[i] = m;
+    c.inv_m[i] = 1.0f / (float)m;
+    c.c_lo[i] = (unsigned long long)ci;
+    c.c_hi[i] = (unsigned long long)(ci >> 64);
+  }
+  c.M_lo = (unsigned long long)M;
+  c.M_hi = (unsigned long long)(M >> 64);
+  c.Mh_lo = (unsigned long long)(M >> 1);
+  c.Mh_hi = (unsigned long long)(M >> 65);
+  c.q_scale = (float)(18446744073709551616.0 / (double)M);
+  return c;
+}
+
+// 256^j mod m_i for the residue kernel (constant memory, once per device)
+cudaError_t upload_crt_table() {
+  int tab[kMaxModuli][6];
+  for (int i = 0; i < kMaxModuli; ++i) {
+    long long p = 1;
+    for (int j = 0; j < 6; ++j) {
+      tab[i][j] = (int)p;
+      p = (p * 256) % kModuli[i];
+    }
+  }
+  return cudaMemcpyToSymbol(c_pow256, tab, sizeof(tab));
+}
+
 cudaError_t launch_slice(const double2 *src, long long lds, int K, const double *urow, int s, int planes,
                          __nv_bfloat16 *dst, long long ldk, long long plane_stride, int *expo, int ncols,
                          cudaStream_t st) {
@@ -893,15 +1443,15 @@ SplitWs split_ws_layout(void *base, int n_g, int depth, int s) {
 // Tiles of one triangle, in bands of `band` column blocks: within a band all
 // row blocks in order, so the ~one wave of tiles that runs at a time shares a
 // few A row blocks and `band` B column blocks through L2.
-std::vector<int2> tri_tiles(int n, int uplo, int band) {
+std::vector<int2> tri_tiles(int n, int uplo, int band, int bn = BN) {
   const int kBand = std::max(1, band);
-  const int nbm = (n + BMT - 1) / BMT, nbn = (n + BN - 1) / BN;
+  const int nbm = (n + BMT - 1) / BMT, nbn = (n + bn - 1) / bn;
   std::vector<int2> out;
   for (int b0 = 0; b0 < nbn; b0 += kBand) {
     const int b1 = std::min(nbn, b0 + kBand);
     for (int bi = 0; bi < nbm; ++bi)
       for (int bj = b0; bj < b1; ++bj) {
-        const bool valid = (uplo == 'U') ? (bi * BMT <= bj * BN + BN - 1) : (bi * BMT + BMT - 1 >= bj * BN);
+        const bool valid = (uplo == 'U') ? (bi * BMT <= bj * bn + bn - 1) : (bi * BMT + BMT - 1 >= bj * bn);
         if (valid) out.push_back(make_int2(bi, bj));
       }
   }
@@ -1012,7 +1562,116 @@ bool hs_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, lon
   return true;
 }
 
+// Moduli form, one H problem (H = W^H X) and one S problem (S = (U W)^H W)
+// over the depth segment [kb0, kb0 + seg): residue planes per modulus W 3,
+// X 3, U W 2; the residue store holds the H tiles' slots, then the S tiles'.
+bool crt_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, long long ldk, int kb0, int seg,
+                  int nkb_all, bool accumulate, int uplo, const __nv_bfloat16 *Wr, const __nv_bfloat16 *Xr,
+                  const __nv_bfloat16 *Yr, const int *expW, const int *expX, const int *expY, double2 *H, double2 *S,
+                  long long ld, const int2 *tiles, long long ntiles, long long tile_begin, long long slot0,
+                  long long slots_per_matrix, unsigned char *store, int nmod, int bits) {
+  for (int k = 0; k < (S ? 2 : 1); ++k) {
+    GemmProblem &q = pr[k];
+    std::memset(&q, 0, sizeof(q));
+    q.M = n_g;
+    q.N = n_g;
+    q.K = seg * BK;
+    q.kb_begin = kb0;
+    q.a_pps = (k == 0) ? 3 : 2;
+    q.b_pps = 3;
+    q.uplo = uplo;
+    q.accumulate = accumulate ? 1 : 0;
+    q.F = 2 * bits;
+    q.expA = (k == 0) ? expW : expY;
+    q.expB = (k == 0) ? expX : expW;
+    q.C = (k == 0) ? H : S;
+    q.ldc = ld;
+    q.n_batch = 1;
+    q.nbm = (n_g + BMT - 1) / BMT;
+    q.nbn = (n_g + BNC - 1) / BNC;
+    q.tile_list = tiles;
+    q.tile_begin = tile_begin + k * ntiles;
+    q.a_nkb = q.b_nkb = (int)(ldk / BK);
+    q.res = store;
+    q.res_base = k * slots_per_matrix + slot0;
+    q.seg_first = kb0 == 0;
+    q.seg_last = kb0 + seg >= nkb_all;
+    const void *a = (k == 0) ? (const void *)Wr : (const void *)Yr;
+    const void *b = (k == 0) ? (const void *)Xr : (const void *)Wr;
+    if (!make_map(&mA[k], a, q.a_nkb, n_g, (long long)q.a_pps * nmod, BM) ||
+        !make_map(&mB[k], b, q.b_nkb, n_g, 3LL * nmod, BNC))
+      return false;
+  }
+  return true;
+}
+
+long long crt_tile_count(int n, int uplo) {
+  // BNC-wide tiles of one triangle (the band only reorders them)
+  return (long long)tri_tiles(n, uplo, 1 << 20, BNC).size();
+}
+
+struct CrtWs {
+  __nv_bfloat16 *Wr, *Xr, *Yr;
+  int *expW, *expX, *expY;
+  unsigned char *store;
+  long long ldk;
+  size_t bytes;
+};
+
+CrtWs crt_ws_layout(void *base, int n_g, int depth, int nmod, long long slots) {
+  CrtWs w;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t r = o;
+    o += (b + 1023) / 1024 * 1024;
+    return r;
+  };
+  w.ldk = round_up(std::max(depth, 1), BK);
+  const size_t plane = (size_t)n_g * w.ldk * sizeof(__nv_bfloat16);
+  const size_t oW = take(plane * 3 * nmod), oX = take(plane * 3 * nmod), oY = take(plane * 2 * nmod);
+  const size_t oe = take(sizeof(int) * 3 * (size_t)n_g);
+  const size_t os = take((size_t)slots * nmod * 65536);
+  w.bytes = o;
+  char *b = (char *)base;
+  w.Wr = (__nv_bfloat16 *)(b + oW);
+  w.Xr = (__nv_bfloat16 *)(b + oX);
+  w.Yr = (__nv_bfloat16 *)(b + oY);
+  w.expW = (int *)(b + oe);
+  w.expX = w.expW + n_g;
+  w.expY = w.expX + n_g;
+  w.store = (unsigned char *)(b + os);
+  return w;
+}
+
 }  // namespace
+
+int choose_moduli(double target_rel_err, int override_moduli, long long K) {
+  if (override_moduli > 0) return std::max(kMinModuli, std::min(override_moduli, kMaxModuli));
+  for (int n = kMinModuli; n <= kMaxModuli; ++n)
+    if (kCrtErr * std::ldexp(1.0, -crt_bits(n, K)) <= target_rel_err) return n;
+  return 0;
+}
+
+SplitPlan split_plan(const hsgen_ctx *ctx, int depth) {
+  SplitPlan p;
+  p.slices = choose_slices(ctx->opt.target_rel_err, ctx->opt.slices);
+  p.scheme = kSchemeSlices;
+  p.nmod = 0;
+  p.bits = 0;
+  const int want = ctx->opt.scheme;
+  if (want == HSGEN_SCHEME_MODULI || (want == HSGEN_SCHEME_AUTO && ctx->opt.slices == 0)) {
+    int n = choose_moduli(ctx->opt.target_rel_err, ctx->opt.moduli, depth);
+    if (n == 0 && want == HSGEN_SCHEME_MODULI) n = kMaxModuli;
+    if (n > 0) {
+      p.scheme = kSchemeModuli;
+      p.nmod = n;
+      p.bits = crt_bits(n, depth);
+    }
+  }
+  return p;
+}
+
+cudaError_t split_upload_tables() { return upload_crt_table(); }
 
 int choose_slices(double target_rel_err, int override_slices) {
   if (override_slices > 0) return std::min(override_slices, kMaxSlices);
@@ -1134,8 +1793,11 @@ hsgen_status split_gemm(hsgen_ctx *ctx, int M, int N, int K, const double2 *P, l
   return HSGEN_OK;
 }
 
-size_t split_workspace_bytes(int n_g, int chunk_depth, int slices) {
-  return split_ws_layout(nullptr, n_g, chunk_depth, slices).bytes;
+size_t split_workspace_bytes(const hsgen_ctx *ctx, int n_g, int chunk_depth) {
+  const SplitPlan pl = split_plan(ctx, chunk_depth);
+  if (pl.scheme == kSchemeModuli)
+    return crt_ws_layout(nullptr, n_g, chunk_depth, pl.nmod, 2 * crt_tile_count(n_g, ctx->opt.uplo)).bytes;
+  return split_ws_layout(nullptr, n_g, chunk_depth, pl.slices).bytes;
 }
 
 hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
@@ -1191,28 +1853,52 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
   }
   const int row_base = ctx->off[a0];
   const int cdepth = ctx->off[a1] - row_base;
-  SplitWs w = split_ws_layout(ws, n_g, cdepth, slices);
-  const long long plane = (long long)n_g * w.ldk;
+  const int uplo = ctx->opt.uplo;
+  const SplitPlan pl = split_plan(ctx, cdepth);
+  const bool crt = pl.scheme == kSchemeModuli;
+  ctx->last_plan = pl;
+  // moduli form: residue planes and the residue store; slice form: slice planes
+  const long long slots = crt ? crt_tile_count(n_g, uplo) : 0;
+  const CrtWs cw = crt ? crt_ws_layout(ws, n_g, cdepth, pl.nmod, 2 * slots) : CrtWs{};
+  const SplitWs w = crt ? SplitWs{} : split_ws_layout(ws, n_g, cdepth, slices);
+  const long long ldk = crt ? cw.ldk : w.ldk;
+  int *expW = crt ? cw.expW : w.expW;
+  // W's slices for X = T W (in the moduli form they sit in X's residue
+  // region, which is written only after X = T W)
+  __nv_bfloat16 *Wsl = crt ? cw.Xr : w.Wsl;
+  const long long plane = (long long)n_g * ldk;
   const unsigned long long tmo = (unsigned long long)ctx->opt.wait_timeout_ns;
   // (1) W slices: planes re, im, -re (used as the left operand of H and the right of X and S)
-  HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, nullptr, slices, 3, w.Wsl, w.ldk, plane, w.expW, n_g, s));
+  HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, nullptr, slices, 3, Wsl, ldk, plane, expW, n_g, s));
   // (2) X_a = T W_a, species by species (up to kMaxProb per launch)
   {
-    hsgen_status st = tapply_split(ctx, n_g, a0, a1, w.Wsl, w.ldk, w.expW, X, ldw, slices, s);
+    hsgen_status st = tapply_split(ctx, n_g, a0, a1, Wsl, ldk, expW, X, ldw, slices, s);
     if (st != HSGEN_OK) return st;
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
-  // (3) X slices (right operand of H) and (U W) slices (left operand of S)
-  HSG_LAUNCH(ctx, launch_slice(X, ldw, cdepth, nullptr, slices, 3, w.Xsl, w.ldk, plane, w.expX, n_g, s));
-  if (S)
-    HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, ctx->d_urow + row_base, slices, 2, w.Ysl, w.ldk, plane, w.expY,
-                                 n_g, s));
+  // (3) the operands of the contraction: X (right operand of H), W (left of
+  // H, right of S) and U W (left of S), as residues or slices
+  const CrtConsts cc = crt ? make_crt(pl.nmod) : CrtConsts{};
+  if (crt) {
+    HSG_LAUNCH(ctx, launch_residue(X, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Xr, ldk, plane, cw.expX, n_g, s));
+    HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Wr, ldk, plane, cw.expW, n_g, s));
+    if (S)
+      HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, ctx->d_urow + row_base, pl.bits, cc, 2, cw.Yr, ldk, plane,
+                                     cw.expY, n_g, s));
+  } else {
+    HSG_LAUNCH(ctx, launch_slice(X, ldw, cdepth, nullptr, slices, 3, w.Xsl, ldk, plane, w.expX, n_g, s));
+    if (S)
+      HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, ctx->d_urow + row_base, slices, 2, w.Ysl, ldk, plane, w.expY,
+                                   n_g, s));
+  }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
   // (4) H = W^H X and S = (U W)^H W over one triangle
   {
-    const int uplo = ctx->opt.uplo;
-    if (ctx->tiles_n != n_g || ctx->tiles_uplo != uplo || ctx->tiles_band != ctx->tile_band) {
-      std::vector<int2> tl = tri_tiles(n_g, uplo, ctx->tile_band);
+    const int bn = crt ? BNC : BN;
+    // tiles in bands of tile_band 64-column blocks (the same width in columns for either tile)
+    const int band = crt ? std::max(1, ctx->tile_band * BN / BNC) : ctx->tile_band;
+    if (ctx->tiles_n != n_g || ctx->tiles_uplo != uplo || ctx->tiles_band != band || ctx->tiles_bn != bn) {
+      std::vector<int2> tl = tri_tiles(n_g, uplo, band, bn);
       if (ctx->d_tiles) cudaFree(ctx->d_tiles);
       ctx->d_tiles = nullptr;
       ctx->tiles_n = -1;
@@ -1221,11 +1907,14 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       ctx->tiles_host = tl;
       ctx->tiles_n = n_g;
       ctx->tiles_uplo = uplo;
-      ctx->tiles_band = ctx->tile_band;
+      ctx->tiles_band = band;
+      ctx->tiles_bn = bn;
       ctx->tiles_count = (long long)tl.size();
     }
-    const int nkb_all = (int)(w.ldk / BK);
-    const int seg_kb = std::max(1, ctx->kseg_blocks);
+    const int nkb_all = (int)(ldk / BK);
+    // moduli form: at most 256 k-blocks per launch (32 chunks of exact FP32
+    // sums keep the epilogue's int32 sums below 2^29)
+    const int seg_kb = crt ? std::max(1, std::min(ctx->kseg_blocks, 256)) : std::max(1, ctx->kseg_blocks);
     const long long per = ctx->tiles_count;
     // one launch: the tiles [t0, t0 + cnt) of the list, of H (and S), over
     // the depth segment [kb0, kb0 + seg)
@@ -1236,18 +1925,28 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       P.s = slices;
       P.status = ctx->d_status;
       P.timeout_ns = tmo;
-      if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, w.ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
-                       w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, slices))
-        return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
       P.nprob = S ? 2 : 1;
       P.ntiles = P.nprob * cnt;
+      if (crt) {
+        P.crt = cc;
+        if (!crt_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, nkb_all, accumulate, uplo, cw.Wr, cw.Xr,
+                          cw.Yr, cw.expW, cw.expX, cw.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, t0,
+                          slots, cw.store, pl.nmod, pl.bits))
+          return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S, moduli)");
+        HSG_LAUNCH(ctx, launch_crt(P, s));
+        return HSGEN_OK;
+      }
+      if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
+                       w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, slices))
+        return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
       HSG_LAUNCH(ctx, launch_gemm(P, s));
       return HSGEN_OK;
     };
     if (!co || (!co->H && !(S && co->S))) {
       // The depth is cut into segments run as separate launches that add into
-      // H and S: shorter tiles keep the CTAs of one wave close together in k,
-      // so the A and B blocks they share stay in L2.
+      // H and S (slices) or into the residue store (moduli): shorter tiles keep
+      // the CTAs of one wave close together in k, so the A and B blocks they
+      // share stay in L2.
       for (int kb0 = 0; kb0 < nkb_all; kb0 += seg_kb) {
         hsgen_status st = launch_seg(0, per, kb0);
         if (st != HSGEN_OK) return st;
@@ -1276,8 +1975,8 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
         if (st != HSGEN_OK) return st;
       }
       // the group holds every tile of columns [c0, c1)
-      const long long c0 = (long long)(tl[t0].y / bandw) * bandw * BN;
-      const long long c1 = std::min<long long>(n_g, (long long)(tl[t1 - 1].y / bandw + 1) * bandw * BN);
+      const long long c0 = (long long)(tl[t0].y / bandw) * bandw * bn;
+      const long long c1 = std::min<long long>(n_g, (long long)(tl[t1 - 1].y / bandw + 1) * bandw * bn);
       HSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, s));
       HSG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev, 0));
       for (int k = 0; k < 2; ++k) {

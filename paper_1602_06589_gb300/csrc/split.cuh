@@ -15,11 +15,19 @@
 namespace hsg {
 
 constexpr int kMaxSlices = 7;
+constexpr int kMinModuli = 10;
 
 // Slices per operand for a target relative error (or the override when > 0).
 int choose_slices(double target_rel_err, int override_slices);
+// Moduli (Ozaki scheme II) for a target relative error at complex depth K
+// (or the override when > 0); 0 when no count up to the maximum meets it.
+int choose_moduli(double target_rel_err, int override_moduli, long long K);
+// The form of one pass over `depth` rows (see SplitPlan).
+SplitPlan split_plan(const hsgen_ctx *ctx, int depth);
 // Bytes of device workspace the split form needs for one pass over `chunk_depth` rows.
-size_t split_workspace_bytes(int n_g, int chunk_depth, int slices);
+size_t split_workspace_bytes(const hsgen_ctx *ctx, int n_g, int chunk_depth);
+// Tables of the moduli form in constant memory (once per device).
+cudaError_t split_upload_tables();
 // Slices the T matrices once per species (called by hsgen_set_atoms in split mode).
 hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices);
 // Host outputs of the last pass: the H/S launches run group by group (groups

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "libhsgen.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENUMERIC = range(7)
 FP64, SPLIT = 0, 1
 S_CONTRACTION, S_LEGENDRE = 0, 1
+SCHEME_AUTO, SCHEME_SLICES, SCHEME_MODULI = 0, 1, 2
 STATUS_NAMES = {0: "HSGEN_OK", 1: "HSGEN_EINVAL", 2: "HSGEN_ENOMEM", 3: "HSGEN_ECUDA", 4: "HSGEN_ETIMEOUT",
                 5: "HSGEN_ENOTSUP", 6: "HSGEN_ENUMERIC"}
 
@@ -33,7 +34,7 @@ _ip = C.POINTER(C.c_int)
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("target_rel_err", C.c_double), ("slices", C.c_int), ("uplo", C.c_int),
                 ("fill_full", C.c_int), ("atom_chunk", C.c_int), ("wait_timeout_ns", C.c_longlong),
-                ("s_form", C.c_int)]
+                ("s_form", C.c_int), ("scheme", C.c_int), ("moduli", C.c_int)]
 
 
 class TypeDesc(C.Structure):
@@ -48,7 +49,8 @@ class Stats(C.Structure):
                 ("precision", C.c_int), ("slices", C.c_int), ("n_kpoints", C.c_int),
                 ("workspace_bytes", C.c_longlong), ("kernel_launches", C.c_longlong), ("s_form", C.c_int),
                 ("ms_s", C.c_double), ("kseg_blocks", C.c_int), ("tile_band", C.c_int),
-                ("ms_upload", C.c_double), ("ms_download", C.c_double)]
+                ("ms_upload", C.c_double), ("ms_download", C.c_double), ("scheme", C.c_int), ("moduli", C.c_int),
+                ("bits", C.c_int), ("products", C.c_int), ("atom_chunks", C.c_int)]
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
@@ -247,7 +249,8 @@ class Generator:
 
     def __init__(self, system, device: int = 0, precision: int = FP64, slices: int = 0,
                  target_rel_err: float = 1e-12, uplo: str = "U", fill_full: bool = False, atom_chunk: int = 0,
-                 wait_timeout_ns: int = 2_000_000_000, s_form: int = S_CONTRACTION):
+                 wait_timeout_ns: int = 2_000_000_000, s_form: int = S_CONTRACTION, scheme: int = SCHEME_AUTO,
+                 moduli: int = 0):
         o = hsgen_default_options()
         o.precision = precision
         o.slices = slices
@@ -257,6 +260,8 @@ class Generator:
         o.atom_chunk = atom_chunk
         o.wait_timeout_ns = wait_timeout_ns
         o.s_form = s_form
+        o.scheme = scheme
+        o.moduli = moduli
         self.device = device
         self.system = system
         self.ctx = hsgen_create(device, o)

@@ -1,5 +1,8 @@
-"""GPU parity of the split-precision (Ozaki BF16 slices on tcgen05) form
-against the oracle, through the C ABI.
+"""GPU parity of the split-precision form (BF16 products on tcgen05) against
+the oracle, through the C ABI, in both of its schemes: slices (Ozaki scheme
+I, s(s+1)/2 products of s BF16 slices per operand) and moduli (Ozaki scheme
+II, one product per modulus of b-bit integer operands, exact by the Chinese
+remainder theorem).
 
 Tolerances (split form): relative Frobenius error <= 1e-11 over
 the written triangle and <= 1e-10 per entry relative to ||w_i|| ||x_j||.
@@ -39,6 +42,13 @@ def mixed_system(seed=3, lmaxes=(2, 4, 0), counts=(2, 1, 2), cell=10.0):
     return make_system(seed, lat, species, list(counts))
 
 
+SCHEMES = ["slices", "moduli"]
+
+
+def scheme_kw(hs, scheme):
+    return {"scheme": hs.SCHEME_SLICES if scheme == "slices" else hs.SCHEME_MODULI}
+
+
 def run_gpu(hs, system, kv, **kw):
     import torch
 
@@ -66,48 +76,99 @@ def check(system, kv, H, S, uplo="U", full=False):
     assert np.all(np.diag(H).imag == 0.0) and np.all(np.diag(S).imag == 0.0)
 
 
-def test_split_config0(hs):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_split_config0(hs, scheme):
     w = make_config(0)
-    H, S, st = run_gpu(hs, w.system, w.kvecs[0])
+    H, S, st = run_gpu(hs, w.system, w.kvecs[0], **scheme_kw(hs, scheme))
     check(w.system, w.kvecs[0], H, S)
     assert st["precision"] == hs.SPLIT and st["slices"] == 6
+    if scheme == "slices":
+        assert st["scheme"] == hs.SCHEME_SLICES and st["products"] == 21
+    else:
+        assert st["scheme"] == hs.SCHEME_MODULI and st["products"] == st["moduli"] and 10 <= st["moduli"] <= 14
 
 
+def test_default_scheme_is_moduli_when_they_meet_the_target(hs):
+    w = make_config(0)
+    _, _, st = run_gpu(hs, w.system, w.kvecs[0])
+    assert st["scheme"] == hs.SCHEME_MODULI and st["products"] < 21
+    _, _, st = run_gpu(hs, w.system, w.kvecs[0], slices=6)  # a slice count forces the slices scheme
+    assert st["scheme"] == hs.SCHEME_SLICES
+    _, _, st = run_gpu(hs, w.system, w.kvecs[0], target_rel_err=1e-15)  # beyond 14 moduli
+    assert st["scheme"] == hs.SCHEME_SLICES and st["slices"] == 7
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("n_g", [1, 7, 129, 300])
-def test_split_ragged_sizes_mixed_lmax(hs, n_g):
+def test_split_ragged_sizes_mixed_lmax(hs, n_g, scheme):
     sysm = mixed_system()
     kv = kpoint_list(sysm.lattice, (0.13, -0.07, 0.21), n_g)
-    H, S, _ = run_gpu(hs, sysm, kv)
+    H, S, _ = run_gpu(hs, sysm, kv, **scheme_kw(hs, scheme))
     check(sysm, kv, H, S)
 
 
-def test_split_gamma_point(hs):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_split_gamma_point(hs, scheme):
     sysm = mixed_system(seed=9)
     kv = kpoint_list(sysm.lattice, (0.0, 0.0, 0.0), 70)
-    H, S, _ = run_gpu(hs, sysm, kv)
+    H, S, _ = run_gpu(hs, sysm, kv, **scheme_kw(hs, scheme))
     check(sysm, kv, H, S)
 
 
-def test_split_lower_full_and_chunked(hs):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_split_lower_full_and_chunked(hs, scheme):
     sysm = mixed_system(seed=11, counts=(3, 2, 2))
     kv = kpoint_list(sysm.lattice, (0.2, 0.1, -0.3), 250)
-    H, S, _ = run_gpu(hs, sysm, kv, uplo="L")
+    kw = scheme_kw(hs, scheme)
+    H, S, _ = run_gpu(hs, sysm, kv, uplo="L", **kw)
     check(sysm, kv, H, S, uplo="L")
-    H, S, _ = run_gpu(hs, sysm, kv, fill_full=True)
+    H, S, _ = run_gpu(hs, sysm, kv, fill_full=True, **kw)
     check(sysm, kv, H, S, full=True)
-    H, S, _ = run_gpu(hs, sysm, kv, atom_chunk=3)
+    H, S, st = run_gpu(hs, sysm, kv, atom_chunk=3, **kw)
+    assert st["atom_chunks"] == 3
     check(sysm, kv, H, S)
 
 
-def test_split_host_pointers(hs):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_split_host_pointers(hs, scheme):
     sysm = mixed_system(seed=13)
     kv = np.ascontiguousarray(kpoint_list(sysm.lattice, (0.1, 0.2, 0.3), 90))
     n = kv.shape[0]
     H = np.zeros((n, n), np.complex128)
     S = np.zeros((n, n), np.complex128)
-    with hs.Generator(sysm, precision=hs.SPLIT) as g:
+    with hs.Generator(sysm, precision=hs.SPLIT, **scheme_kw(hs, scheme)) as g:
         hs.hsgen_build_HS(g.ctx, n, kv.ctypes.data, H.ctypes.data, S.ctypes.data, n, 0)
     check(sysm, kv, H.T, S.T)
+
+
+def test_moduli_error_follows_the_bits(hs):
+    """Moduli form: the integer product is exact, so the error is that of
+    rounding the operands to b-bit integers: it falls with every added
+    modulus (about 4 bits each) and stays below the library's error model
+    32 * 2^-b, which chooses the count."""
+    w = make_config(0)
+    kv = w.kvecs[0]
+    errs = []
+    for n in (10, 11, 12, 13, 14):
+        H, S, st = run_gpu(hs, w.system, kv, scheme=hs.SCHEME_MODULI, moduli=n)
+        assert st["moduli"] == n and st["products"] == n
+        (hf, _), (sf, _), _ = errors(w.system, kv, H, S)
+        err = max(hf, sf)
+        assert err <= 32.0 * 2.0 ** -st["bits"], (n, st["bits"], err)
+        errs.append((st["bits"], err))
+    for (b0, e0), (b1, e1) in zip(errs, errs[1:]):
+        assert b1 > b0 and (e1 < e0 or e1 < 1e-14), errs
+
+
+def test_moduli_across_many_depth_segments(hs, monkeypatch):
+    """One depth segment of 64 rows per launch (41 launches at 16 atoms /
+    N_G 3000): the residues of every segment add up modulo each m_i in the
+    residue store, and only the last launch writes H and S."""
+    monkeypatch.setenv("HSGEN_KSEG_BLOCKS", "1")
+    w = make_config(1)
+    H, S, st = run_gpu(hs, w.system, w.kvecs[0], scheme=hs.SCHEME_MODULI)
+    assert st["kseg_blocks"] == 1 and st["scheme"] == hs.SCHEME_MODULI
+    check(w.system, w.kvecs[0], H, S)
 
 
 @pytest.mark.parametrize("uplo,s_form,chunk", [("U", "S_CONTRACTION", 0), ("L", "S_CONTRACTION", 0),
@@ -164,7 +225,8 @@ def test_split_error_falls_with_slices(hs):
     assert errs[-1] < 2e-14, errs
 
 
-def test_split_complex_T_override(hs):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_split_complex_T_override(hs, scheme):
     """A genuinely complex Hermitian T exercises the imaginary half of X = T W."""
     sysm = mixed_system(seed=21)
     rng = np.random.default_rng(3)
@@ -173,13 +235,14 @@ def test_split_complex_T_override(hs):
         A = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
         ty.T_override = 0.5 * (A + A.conj().T)
     kv = kpoint_list(sysm.lattice, (0.1, 0.0, 0.2), 140)
-    H, S, _ = run_gpu(hs, sysm, kv)
+    H, S, _ = run_gpu(hs, sysm, kv, **scheme_kw(hs, scheme))
     check(sysm, kv, H, S)
 
 
-def test_split_config1(hs):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_split_config1(hs, scheme):
     w = make_config(1)
-    H, S, _ = run_gpu(hs, w.system, w.kvecs[0])
+    H, S, _ = run_gpu(hs, w.system, w.kvecs[0], **scheme_kw(hs, scheme))
     check(w.system, w.kvecs[0], H, S)
 
 
@@ -193,13 +256,13 @@ def test_split_matches_fp64_form(hs):
     assert np.linalg.norm((Ss - Sd)[m]) <= 1e-11 * np.linalg.norm(Sd[m])
 
 
-def sampled_check(hs, cfg, kidx=0, n_samp=14, seed=0):
+def sampled_check(hs, cfg, kidx=0, n_samp=14, seed=0, **kw):
     import torch
 
     w = make_config(cfg)
     kv = w.kvecs[kidx]
     n = kv.shape[0]
-    with hs.Generator(w.system, precision=hs.SPLIT) as g:
+    with hs.Generator(w.system, precision=hs.SPLIT, **kw) as g:
         H, S = g.build(torch.from_numpy(kv).cuda())
         torch.cuda.synchronize()
         rng = np.random.default_rng(seed)
@@ -228,8 +291,9 @@ def sampled_check(hs, cfg, kidx=0, n_samp=14, seed=0):
     assert per_h <= PER_ENTRY and per_s <= PER_ENTRY, (per_h, per_s)
 
 
-def test_split_config2_sampled(hs):
-    sampled_check(hs, 2)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_split_config2_sampled(hs, scheme):
+    sampled_check(hs, 2, **scheme_kw(hs, scheme))
 
 
 def test_split_config3_one_kpoint_sampled(hs):
