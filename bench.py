@@ -39,6 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H+S build s/k-pt & eff TFLOP/s: split-prec vs FP64 on 1 GB300 @<=1e-11 err"
+SCHEMES = {"auto": 0, "slices": 1, "moduli": 2}
 
 
 def _peaks():
@@ -577,6 +578,11 @@ def main():
     ap.add_argument("--form", choices=["split", "fp64"], default="split")
     ap.add_argument("--config", type=int, default=4)
     ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--moduli", type=int, default=0, help="split form, moduli scheme: moduli count (0: from the target)")
+    ap.add_argument("--scheme", choices=sorted(SCHEMES), default="auto",
+                    help="split form: slices (Ozaki I), moduli (Ozaki II) or auto (moduli when they meet the target)")
+    ap.add_argument("--target", type=float, default=1e-11,
+                    help="split form: relative error the slice or moduli count is chosen for (the metric's 1e-11)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-columns", type=int, default=384)
@@ -652,7 +658,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     s_form = hsgen.S_LEGENDRE if args.s_form == "legendre" else hsgen.S_CONTRACTION
-    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form)
+    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form,
+                        target_rel_err=args.target, scheme=SCHEMES[args.scheme], moduli=args.moduli)
     kv = torch.from_numpy(kv_host).to(dev)
     H = torch.zeros((n, n), dtype=torch.complex128, device=dev)
     S = torch.zeros_like(H)
@@ -714,6 +721,13 @@ def main():
                    else "contraction",
                    "l_nonsph": args.l_nonsph if args.l_nonsph >= 0 else "l_max",
                    "slices": st["slices"] if precision == hsgen.SPLIT else None,
+                   "scheme": ({1: "slices (Ozaki I)", 2: "moduli (Ozaki II)"}.get(st["scheme"])
+                              if precision == hsgen.SPLIT else None),
+                   "moduli": st["moduli"] if precision == hsgen.SPLIT else None,
+                   "operand_bits": st["bits"] if precision == hsgen.SPLIT else None,
+                   "bf16_products_per_fp64_product": st["products"] if precision == hsgen.SPLIT else None,
+                   "target_rel_err": args.target if precision == hsgen.SPLIT else None,
+                   "atom_chunks": st["atom_chunks"],
                    "schedule": ({"kseg_blocks": tuned["kseg_blocks"], "tile_band": tuned["tile_band"],
                                  "autotuned": not args.no_autotune} if precision == hsgen.SPLIT else None),
                    "l2": "working set >> L2 (no flush needed)", "parallelism": f"k-point replicas x{world}"},
