@@ -364,18 +364,19 @@ def reduce_bench(args, w):
     flops = (8.0 / 3.0 + 8.0) * float(n) ** 3  # Cholesky n^3/3 + two solves n^3/2 complex MACs each, 8 flops per MAC
     peaks = _peaks()
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-    fp64_peak = bf16 * 1.25 / 2250.0
+    p64, _ = _fp64_peak()
+    fp64_peak = p64 or bf16 * 1.25 / 2250.0
     achieved = flops / t / 1e12
-    # split form (upper triangle): blocks of 512, FP64 diagonal blocks, updates as
-    # 7-slice BF16 products (28 slice pairs); the FP64 library form otherwise
+    # blocks of 128 rows: FP64 tile kernels for the diagonal blocks; products as
+    # 7-slice BF16 products (28 slice pairs, split form) or FP64 DMMA (FP64 form)
     split = args.form == "split"
     line = {"metric": "generalized-eigenproblem reduction (Cholesky of S, H~ = U^-H H U^-1), s/k-point",
             "impl": "reduce", "value": t, "unit": "s/k-point", "n_gpus": 1, "steps": args.steps,
             "warmup": max(1, args.warmup), "higher_is_better": False, "dtype": "bf16-split/f64" if split else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(args.config, w), "interstitial": "stand-in S + I, H + diag(|K|^2)",
-                       "form": "split: FP64 diagonal blocks, 7-slice BF16 updates" if split
-                       else "FP64: cuSOLVER ZPOTRF + 2 cuBLAS ZTRSM"},
+                       "form": "split: FP64 tile kernels on the diagonal blocks, 7-slice BF16 products" if split
+                       else "FP64: FP64 tile kernels on the diagonal blocks, FP64 DMMA products"},
             "build_s_per_kpoint": build_s, "fp64_equivalent_tflops": achieved,
             "roofline": ({"bound": "tensor", "achieved": flops * 28 / t / 1e12, "peak": bf16, "unit": "TFLOP/s",
                           "frac": flops * 28 / t / 1e12 / bf16, "traffic": None,
@@ -383,8 +384,9 @@ def reduce_bench(args, w):
                           "peak_source": "measured bf16 sustained"} if split else
                          {"bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                           "frac": achieved / fp64_peak, "traffic": None,
-                          "kernel": "cuSOLVER ZPOTRF + 2 cuBLAS ZTRSM (FP64)",
-                          "peak_source": "measured bf16 sustained x nominal fp64/bf16 ratio"})}
+                          "kernel": "whole reduction in FP64 (DMMA products, FP64 tile kernels)",
+                          "peak_source": "measured FP64 DMMA loop" if p64 else
+                                         "measured bf16 sustained x nominal fp64/bf16 ratio"})}
     print(json.dumps(line), flush=True)
 
 

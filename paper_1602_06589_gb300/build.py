@@ -34,7 +34,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "hsgen.h")]
+    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "hsgen.h"),
+                                                                   os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:
@@ -68,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, err in results:
             sys.stderr.write(err)
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart", "-lcuda", "-lcublas", "-lcusolver"],
+    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

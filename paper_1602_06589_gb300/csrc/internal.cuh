@@ -90,9 +90,7 @@ struct hsgen_ctx {
   hsg::Workspace ws_main;           // W, X, radial factors, kvec copy, split slices
   hsg::Workspace ws_out;            // device H/S staging when the caller passes host pointers
   hsg::Workspace ws_leg;            // S in the Legendre form: coordinates, structure factors, tables
-  hsg::Workspace ws_red;            // generalized-eigenproblem reduction: factorization workspace, status
-  void *blas = nullptr;             // cublasHandle_t of the reduction
-  void *solver = nullptr;           // cusolverDnHandle_t of the reduction
+  hsg::Workspace ws_red;            // generalized-eigenproblem reduction: block inverses, products, status
   int *h_info = nullptr;            // pinned host copy of the factorization status
   int split_slices = 0;             // slices the species' T were cut into
   int *d_status = nullptr;          // device status word of the split kernels
@@ -197,6 +195,10 @@ cudaError_t launch_tapply_fp64(int dpad, int n_g, const double2 *T, const int *a
 cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *X, const double *urow,
                            long long ldw, double2 *H, double2 *S, long long ld, int uplo, int accumulate,
                            cudaStream_t s);
+// C (+)= (+-) P^H Q in FP64 (DMMA): P is K x M, Q is K x N (complex, column-major), C is M x N;
+// uplo 'U': only the entries i <= j (diagonal imaginary parts set to 0); C must not overlap P or Q.
+cudaError_t launch_gemm_fp64(int M, int N, int K, const double2 *P, long long ldp, const double2 *Q, long long ldq,
+                             double2 *C, long long ldc, int uplo, int accumulate, int negate, cudaStream_t s);
 // Mirror the written triangle into the other one (fill_full) and clear diagonal imaginary parts.
 cudaError_t launch_mirror(int n_g, double2 *M, long long ld, int uplo, cudaStream_t s);
 

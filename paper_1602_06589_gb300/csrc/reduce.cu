@@ -1,17 +1,27 @@
 // reduce.cu -- hand-off of H and S to the generalized eigensolver (Sec. 2.3,
 // Eq. matrix_kohnsham: H c = eps S c with H, S Hermitian and S positive
-// definite). S is factored in FP64, S = U^H U (opt.uplo 'U') or S = L L^H
-// ('L'), in place in its triangle, and H is reduced in place to the standard
-// problem H~ y = eps y, c = U^-1 y:
+// definite). S is factored, S = U^H U (opt.uplo 'U') or S = L L^H ('L'), in
+// place in its triangle, and H is reduced in place to the standard problem
+// H~ y = eps y, c = U^-1 y:
 //   H~ = U^-H H U^-1   (= L^-1 H L^-H, the same matrix: the factor is unique),
-// written in full and exactly Hermitian. The factorization (ZPOTRF) and the
-// two triangular solves (ZTRSM) are cuSOLVER / cuBLAS calls in FP64; this file
-// adds the checks, the Hermitian fill of H before the solves and the
-// symmetrisation of the result.
-#include <cublas_v2.h>
-#include <cusolverDn.h>
-
+// written in full and exactly Hermitian.
+//
+// Everything runs in this library's kernels, blocked by nb rows (default
+// 128), right-looking on the upper factor:
+//   for each block row k:  U_kk = chol(S_kk) and D_k = U_kk^-1   (FP64, tiles of 32)
+//                          U_k,rest = D_k^H S_k,rest              (a product)
+//                          S_rest -= U_k,rest^H U_k,rest          (a product, upper triangle)
+// and the two triangular solves Y = U^-H H, H~ = U^-H Y^H by block rows:
+//   X_k = D_k^H B_k, B_rest -= U_k,rest^H X_k.
+// The products run as 7-slice BF16 products on the tensor cores (split form,
+// ~2e-15 relative, FP64's level) or as FP64 DMMA products (FP64 form); the
+// diagonal blocks are factored and inverted in FP64 by tile kernels (32 x 32
+// tiles: Cholesky of the diagonal tile and its inverse in one CTA, the row of
+// tiles right of it, the trailing tiles, then the block's inverse by back
+// substitution over tiles). The lower-triangle layout is factored through a
+// conjugate-transposed copy of S in the upper layout.
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -21,6 +31,8 @@
 
 namespace hsg {
 namespace {
+
+constexpr int TS = 32;  // tile of the diagonal-block kernels
 
 // mode 0: the triangle opposite `uplo` takes the conjugate transpose of the
 // `uplo` triangle; mode 1: both triangles take the average (M + M^H) / 2;
@@ -71,65 +83,296 @@ cudaError_t launch_hermitian(int n, double2 *M, long long ld, int uplo, int mode
   return cudaGetLastError();
 }
 
-hsgen_status blas_err(hsgen_ctx *ctx, int code, const char *what) {
-  return set_err(ctx, HSGEN_ECUDA, std::string(what) + " failed (status " + std::to_string(code) + ")");
+// Cholesky of one diagonal tile (nt <= 32 rows, upper: A = U^H U) in place
+// and its inverse Tinv = U^-1 (32 x 32, upper, zeros below). Only the upper
+// triangle of the tile is read and written. A pivot that is not positive (or
+// not finite) records the global row in `info` (the smallest one wins) and is
+// replaced by 1 so that the rest stays finite.
+__global__ void __launch_bounds__(TS * TS) chol_tile_kernel(double2 *A, long long ld, int nt, double2 *Tinv,
+                                                           int row0, int *info) {
+  __shared__ double2 a[TS][TS + 1];  // a[c][r] = A(r, c)
+  __shared__ double2 x[TS][TS + 1];  // x[c][r] = Tinv(r, c)
+  const int r = threadIdx.x, c = threadIdx.y;
+  a[c][r] = (r < nt && c < nt && r <= c) ? A[(size_t)c * ld + r] : make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int j = 0; j < nt; ++j) {
+    if (r == 0 && c == 0) {
+      double d = a[j][j].x;
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicMin(info, row0 + j + 1);
+        d = 1.0;
+      }
+      a[j][j] = make_double2(sqrt(d), 0.0);
+    }
+    __syncthreads();
+    if (r == j && c > j && c < nt) {  // row j of U
+      const double inv = 1.0 / a[j][j].x;
+      a[c][j] = make_double2(a[c][j].x * inv, a[c][j].y * inv);
+    }
+    __syncthreads();
+    if (r > j && r <= c && c < nt) {  // S(r, c) -= conj(U(j, r)) U(j, c)
+      const double2 u = a[r][j], v = a[c][j];
+      a[c][r].x -= u.x * v.x + u.y * v.y;
+      a[c][r].y -= u.x * v.y - u.y * v.x;
+    }
+    __syncthreads();
+  }
+  // inverse: column c of X = U^-1 by back substitution (one thread per column)
+  if (c == 0 && r < TS) {
+    const int col = r;
+    for (int i = 0; i < TS; ++i) x[col][i] = make_double2(0.0, 0.0);
+    if (col < nt) {
+      x[col][col] = make_double2(1.0 / a[col][col].x, 0.0);
+      for (int i = col - 1; i >= 0; --i) {
+        double sr = 0.0, si = 0.0;
+        for (int k = i + 1; k <= col; ++k) {  // U(i, k) X(k, col)
+          const double2 u = a[k][i], v = x[col][k];
+          sr += u.x * v.x - u.y * v.y;
+          si += u.x * v.y + u.y * v.x;
+        }
+        const double inv = 1.0 / a[i][i].x;
+        x[col][i] = make_double2(-sr * inv, -si * inv);
+      }
+    }
+  }
+  __syncthreads();
+  if (r < nt && c < nt && r <= c) A[(size_t)c * ld + r] = a[c][r];
+  Tinv[c * TS + r] = x[c][r];
 }
 
-// Split form of the reduction (upper triangle): blocks of kRedBlock rows;
-// the diagonal blocks are factored and solved in FP64 (cuSOLVER / cuBLAS),
-// the updates that carry ~all the flops run as BF16-slice products on the
-// tensor cores (split_gemm) with kRedSlices slices, which give products to
-// ~2e-15 relative, FP64's level.
-// 256: at N_G 12 000, 1.13 s against 1.16 (192), 1.18 (128), 1.41 (512), 2.04 s (1024): smaller
-// blocks shrink the FP64 diagonal-block solves, larger ones the updates' short depth
-constexpr int kRedBlock = 256;  // default; HSGEN_REDUCE_BLOCK (64..4096, rounded to 64) overrides it
+// Row of tiles right of diagonal tile j: A_jc <- Tinv_j^H A_jc (blockIdx.x = c - j - 1).
+__global__ void __launch_bounds__(TS * TS) tile_row_kernel(double2 *A, long long ld, int kb, int j,
+                                                          const double2 *Tinv) {
+  __shared__ double2 t[TS][TS + 1], b[TS][TS + 1];
+  const int r = threadIdx.x, c = threadIdx.y;
+  const int tc = j + 1 + blockIdx.x;
+  const int rows = min(TS, kb - j * TS), cols = min(TS, kb - tc * TS);
+  double2 *blk = A + (size_t)(tc * TS) * ld + j * TS;
+  t[c][r] = Tinv[c * TS + r];
+  b[c][r] = (r < rows && c < cols) ? blk[(size_t)c * ld + r] : make_double2(0.0, 0.0);
+  __syncthreads();
+  double sr = 0.0, si = 0.0;
+  for (int k = 0; k <= r; ++k) {  // conj(Tinv(k, r)) B(k, c)
+    const double2 u = t[r][k], v = b[c][k];
+    sr += u.x * v.x + u.y * v.y;
+    si += u.x * v.y - u.y * v.x;
+  }
+  if (r < rows && c < cols) blk[(size_t)c * ld + r] = make_double2(sr, si);
+}
+
+// Trailing tiles of the diagonal block: A_rc -= A_jr^H A_jc for j < r <= c
+// (blockIdx.x enumerates the pairs); a diagonal tile keeps its lower part.
+__global__ void __launch_bounds__(TS * TS) tile_update_kernel(double2 *A, long long ld, int kb, int j) {
+  __shared__ double2 p[TS][TS + 1], q[TS][TS + 1];
+  const int r = threadIdx.x, c = threadIdx.y;
+  const int nt = (kb + TS - 1) / TS;
+  int idx = blockIdx.x, tr = j + 1, tc = j + 1;
+  for (tc = j + 1; tc < nt; ++tc) {  // pairs (tr, tc), j < tr <= tc, column by column
+    const int cnt = tc - j;
+    if (idx < cnt) {
+      tr = j + 1 + idx;
+      break;
+    }
+    idx -= cnt;
+  }
+  const int rows = min(TS, kb - tr * TS), cols = min(TS, kb - tc * TS), kd = min(TS, kb - j * TS);
+  const double2 *Pj = A + (size_t)(tr * TS) * ld + j * TS;  // A_jr
+  const double2 *Qj = A + (size_t)(tc * TS) * ld + j * TS;  // A_jc
+  p[c][r] = (r < kd && c < rows) ? Pj[(size_t)c * ld + r] : make_double2(0.0, 0.0);
+  q[c][r] = (r < kd && c < cols) ? Qj[(size_t)c * ld + r] : make_double2(0.0, 0.0);
+  __syncthreads();
+  double sr = 0.0, si = 0.0;
+  for (int k = 0; k < kd; ++k) {  // conj(P(k, r)) Q(k, c)
+    const double2 u = p[r][k], v = q[c][k];
+    sr += u.x * v.x + u.y * v.y;
+    si += u.x * v.y - u.y * v.x;
+  }
+  if (r < rows && c < cols && (tr != tc || r <= c)) {
+    double2 *dst = A + (size_t)(tc * TS + c) * ld + tr * TS + r;
+    const double2 o = *dst;
+    *dst = make_double2(o.x - sr, o.y - si);
+  }
+}
+
+// Inverse D = U^-1 of the factored diagonal block (kb x kb upper, tiles of
+// 32): column of tiles c = blockIdx.x, from the diagonal tile up:
+// D_cc = Tinv_c, D_rc = -Tinv_r sum_{r < k <= c} U_rk D_kc. D: ldd = kb,
+// zeros below the diagonal.
+__global__ void __launch_bounds__(TS * TS) block_inverse_kernel(const double2 *A, long long ld, int kb,
+                                                               const double2 *Tinv, double2 *D, int ldd) {
+  __shared__ double2 u[TS][TS + 1], v[TS][TS + 1];
+  const int r = threadIdx.x, c = threadIdx.y;
+  const int nt = (kb + TS - 1) / TS;
+  const int tc = blockIdx.x;
+  const int cols = min(TS, kb - tc * TS);
+  for (int tr = nt - 1; tr > tc; --tr) {  // tiles below the diagonal: zero
+    const int rows = min(TS, kb - tr * TS);
+    if (r < rows && c < cols) D[(size_t)(tc * TS + c) * ldd + tr * TS + r] = make_double2(0.0, 0.0);
+  }
+  if (r < TS && c < cols && tc * TS + r < kb) {
+    D[(size_t)(tc * TS + c) * ldd + tc * TS + r] = Tinv[(size_t)tc * TS * TS + c * TS + r];
+  }
+  __syncthreads();
+  for (int tr = tc - 1; tr >= 0; --tr) {
+    // acc = sum_{tr < k <= tc} U_{tr,k} D_{k,tc}
+    double sr = 0.0, si = 0.0;
+    for (int tk = tr + 1; tk <= tc; ++tk) {
+      const int kd = min(TS, kb - tk * TS);
+      u[c][r] = (c < kd) ? A[(size_t)(tk * TS + c) * ld + tr * TS + r] : make_double2(0.0, 0.0);  // U(tr*32+r, tk*32+c)
+      v[c][r] = (r < kd && c < cols) ? D[(size_t)(tc * TS + c) * ldd + tk * TS + r] : make_double2(0.0, 0.0);
+      __syncthreads();
+      for (int k = 0; k < kd; ++k) {  // U(r, k) D(k, c)
+        const double2 a = u[k][r], b = v[c][k];
+        sr += a.x * b.x - a.y * b.y;
+        si += a.x * b.y + a.y * b.x;
+      }
+      __syncthreads();
+    }
+    v[c][r] = make_double2(sr, si);  // the sum (both tiles are free again)
+    u[c][r] = Tinv[(size_t)tr * TS * TS + c * TS + r];
+    __syncthreads();
+    double xr = 0.0, xi = 0.0;
+    for (int k = r; k < TS; ++k) {  // -Tinv(r, k) acc(k, c), Tinv upper
+      const double2 a = u[k][r], b = v[c][k];
+      xr -= a.x * b.x - a.y * b.y;
+      xi -= a.x * b.y + a.y * b.x;
+    }
+    if (c < cols) D[(size_t)(tc * TS + c) * ldd + tr * TS + r] = make_double2(xr, xi);
+    __syncthreads();
+  }
+}
+
+// Lower layout: dst(j, i) = conj(src(i, j)) for i >= j (the upper triangle of
+// dst from the lower triangle of src), or, with to_lower, dst(i, j) =
+// conj(src(j, i)) for i >= j (the lower triangle of dst from the upper of src).
+__global__ void tri_transpose_kernel(int n, const double2 *src, double2 *dst, long long ld, int to_lower) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n || i < j) return;
+  if (to_lower) {
+    const double2 v = src[(size_t)i * ld + j];
+    dst[(size_t)j * ld + i] = make_double2(v.x, -v.y);
+  } else {
+    const double2 v = src[(size_t)j * ld + i];
+    dst[(size_t)i * ld + j] = make_double2(v.x, -v.y);
+  }
+}
+
+hsgen_status red_err(hsgen_ctx *ctx, cudaError_t e, const char *what) { return cuda_err(ctx, e, what); }
+
+constexpr int kRedBlock = 128;  // default; HSGEN_REDUCE_BLOCK (32..1024, multiple of 32) overrides it
 constexpr int kRedSlices = 7;
 
 int reduce_block() {
   int nb = kRedBlock;
-  if (const char *e = std::getenv("HSGEN_REDUCE_BLOCK")) nb = std::max(64, std::min(4096, std::atoi(e))) / 64 * 64;
+  if (const char *e = std::getenv("HSGEN_REDUCE_BLOCK")) nb = std::max(32, std::min(1024, std::atoi(e))) / 32 * 32;
   return nb;
 }
 
-// S = U^H U in place (upper triangle), right-looking: U11 = chol(A11),
-// U12 = U11^-H A12, A22 -= U12^H U12.
-hsgen_status potrf_split(hsgen_ctx *ctx, int n, int nb, double2 *S, long long ld, cuDoubleComplex *work, int lwork,
-                         int *d_info, void *gws, cudaStream_t s) {
-  cublasHandle_t blas = (cublasHandle_t)ctx->blas;
-  cusolverDnHandle_t solver = (cusolverDnHandle_t)ctx->solver;
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0);
+struct RedWs {
+  double2 *Dinv;   // inverses of the diagonal blocks, nb x nb each (ld nb), block k at k * nb * nb
+  double2 *Tinv;   // tile inverses of the block being factored (nb / 32 tiles of 32 x 32)
+  double2 *tmp;    // FP64 form: product output before it is copied back (nb x n)
+  double2 *Scopy;  // lower layout: S in the upper layout
+  int *info;
+  void *gws;       // split products
+  size_t bytes;
+};
+
+RedWs red_layout(void *base, int n, long long ld, int nb, bool split, bool lower) {
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const int nblk = (n + nb - 1) / nb;
+  RedWs w;
+  size_t o = 0;
+  char *b = (char *)base;
+  w.Dinv = (double2 *)(b + o);
+  o += al(sizeof(double2) * (size_t)nblk * nb * nb);
+  w.Tinv = (double2 *)(b + o);
+  o += al(sizeof(double2) * (size_t)((nb + TS - 1) / TS) * TS * TS);
+  w.tmp = (double2 *)(b + o);
+  o += split ? 0 : al(sizeof(double2) * (size_t)nb * n);
+  w.Scopy = (double2 *)(b + o);
+  o += lower ? al(sizeof(double2) * (size_t)ld * n) : 0;
+  w.info = (int *)(b + o);
+  o += al(sizeof(int));
+  w.gws = b + o;
+  o += split ? split_gemm_ws_bytes(n, n, std::min(n, nb), kRedSlices) : 0;
+  w.bytes = o;
+  return w;
+}
+
+// C (+)= (+-) P^H Q (P: K x M, Q: K x N) in the chosen form. In the split
+// form C may be Q itself (the operands are sliced before the product is
+// formed); in the FP64 form an in-place product goes through w.tmp.
+hsgen_status product(hsgen_ctx *ctx, bool split, int M, int N, int K, const double2 *P, long long ldp,
+                     const double2 *Q, long long ldq, double2 *C, long long ldc, int uplo, bool accumulate,
+                     bool negate, const RedWs &w, cudaStream_t s) {
+  if (split)
+    return split_gemm(ctx, M, N, K, P, ldp, Q, ldq, C, ldc, uplo, accumulate, negate, kRedSlices, w.gws, s);
+  if (C == Q) {
+    HSG_LAUNCH(ctx, launch_gemm_fp64(M, N, K, P, ldp, Q, ldq, w.tmp, M, uplo, 0, negate ? 1 : 0, s));
+    HSG_CUDA(ctx, cudaMemcpy2DAsync(C, sizeof(double2) * ldc, w.tmp, sizeof(double2) * M, sizeof(double2) * M, N,
+                                    cudaMemcpyDeviceToDevice, s));
+    return HSGEN_OK;
+  }
+  HSG_LAUNCH(ctx, launch_gemm_fp64(M, N, K, P, ldp, Q, ldq, C, ldc, uplo, accumulate ? 1 : 0, negate ? 1 : 0, s));
+  return HSGEN_OK;
+}
+
+// U_kk = chol(S_kk) in place and D = U_kk^-1 (kb x kb, ld kb), FP64 tile kernels.
+hsgen_status factor_diag(hsgen_ctx *ctx, double2 *Skk, long long ld, int kb, int row0, double2 *D, const RedWs &w,
+                         cudaStream_t s) {
+  const int nt = (kb + TS - 1) / TS;
+  const dim3 blk(TS, TS);
+  for (int j = 0; j < nt; ++j) {
+    const int tj = std::min(TS, kb - j * TS);
+    double2 *Ajj = Skk + (size_t)(j * TS) * ld + j * TS;
+    chol_tile_kernel<<<1, blk, 0, s>>>(Ajj, ld, tj, w.Tinv + (size_t)j * TS * TS, row0 + j * TS, w.info);
+    HSG_LAUNCH(ctx, cudaGetLastError());
+    if (j + 1 < nt) {
+      tile_row_kernel<<<nt - 1 - j, blk, 0, s>>>(Skk, ld, kb, j, w.Tinv + (size_t)j * TS * TS);
+      HSG_LAUNCH(ctx, cudaGetLastError());
+      const int pairs = (nt - 1 - j) * (nt - j) / 2;
+      tile_update_kernel<<<pairs, blk, 0, s>>>(Skk, ld, kb, j);
+      HSG_LAUNCH(ctx, cudaGetLastError());
+    }
+  }
+  block_inverse_kernel<<<nt, blk, 0, s>>>(Skk, ld, kb, w.Tinv, D, kb);
+  HSG_LAUNCH(ctx, cudaGetLastError());
+  return HSGEN_OK;
+}
+
+// S = U^H U in place (upper triangle), right-looking by blocks of nb.
+hsgen_status potrf_blocked(hsgen_ctx *ctx, bool split, int n, int nb, double2 *S, long long ld, const RedWs &w,
+                           cudaStream_t s) {
   for (int k = 0, blk = 0; k < n; k += nb, ++blk) {
     const int kb = std::min(nb, n - k), m = n - k - kb;
-    cuDoubleComplex *Skk = (cuDoubleComplex *)(S + k + (size_t)k * ld);
-    cusolverStatus_t se = cusolverDnZpotrf(solver, CUBLAS_FILL_MODE_UPPER, kb, Skk, (int)ld, work, lwork, d_info + blk);
-    if (se != CUSOLVER_STATUS_SUCCESS) return blas_err(ctx, (int)se, "cusolverDnZpotrf");
+    double2 *Skk = S + k + (size_t)k * ld;
+    double2 *D = w.Dinv + (size_t)blk * nb * nb;
+    hsgen_status st = factor_diag(ctx, Skk, ld, kb, k, D, w, s);
+    if (st != HSGEN_OK) return st;
     if (m == 0) break;
     double2 *U12 = S + k + (size_t)(k + kb) * ld;
-    cublasStatus_t be = cublasZtrsm(blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT,
-                                    kb, m, &one, Skk, (int)ld, (cuDoubleComplex *)U12, (int)ld);
-    if (be != CUBLAS_STATUS_SUCCESS) return blas_err(ctx, (int)be, "cublasZtrsm (panel)");
-    hsgen_status st = split_gemm(ctx, m, m, kb, U12, ld, U12, ld, S + (k + kb) + (size_t)(k + kb) * ld, ld, 'U',
-                                 true, true, kRedSlices, gws, s);
+    st = product(ctx, split, kb, m, kb, D, kb, U12, ld, U12, ld, 0, false, false, w, s);  // U12 = D^H S12
+    if (st != HSGEN_OK) return st;
+    st = product(ctx, split, m, m, kb, U12, ld, U12, ld, S + (k + kb) + (size_t)(k + kb) * ld, ld, 'U', true, true,
+                 w, s);  // S22 -= U12^H U12
     if (st != HSGEN_OK) return st;
   }
   return HSGEN_OK;
 }
 
-// U^H X = B in place on B (n x n), U upper triangular; by block rows:
-// X_k = U_kk^-H B_k, then B_rest -= U_{k,rest}^H X_k.
-hsgen_status solve_left_split(hsgen_ctx *ctx, int n, int nb, const double2 *U, double2 *B, long long ld, void *gws,
-                              cudaStream_t s) {
-  cublasHandle_t blas = (cublasHandle_t)ctx->blas;
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0);
-  for (int k = 0; k < n; k += nb) {
+// U^H X = B in place on B (n x n), U upper triangular with block inverses D_k:
+// X_k = D_k^H B_k, then B_rest -= U_{k,rest}^H X_k.
+hsgen_status solve_left_blocked(hsgen_ctx *ctx, bool split, int n, int nb, const double2 *U, double2 *B,
+                                long long ld, const RedWs &w, cudaStream_t s) {
+  for (int k = 0, blk = 0; k < n; k += nb, ++blk) {
     const int kb = std::min(nb, n - k), m = n - k - kb;
-    cublasStatus_t be = cublasZtrsm(blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT,
-                                    kb, n, &one, (const cuDoubleComplex *)(U + k + (size_t)k * ld), (int)ld,
-                                    (cuDoubleComplex *)(B + k), (int)ld);
-    if (be != CUBLAS_STATUS_SUCCESS) return blas_err(ctx, (int)be, "cublasZtrsm (block)");
+    const double2 *D = w.Dinv + (size_t)blk * nb * nb;
+    hsgen_status st = product(ctx, split, kb, n, kb, D, kb, B + k, ld, B + k, ld, 0, false, false, w, s);
+    if (st != HSGEN_OK) return st;
     if (m == 0) break;
-    hsgen_status st = split_gemm(ctx, m, n, kb, U + k + (size_t)(k + kb) * ld, ld, B + k, ld, B + k + kb, ld, 0,
-                                 true, true, kRedSlices, gws, s);
+    st = product(ctx, split, m, n, kb, U + k + (size_t)(k + kb) * ld, ld, B + k, ld, B + k + kb, ld, 0, true, true,
+                 w, s);
     if (st != HSGEN_OK) return st;
   }
   return HSGEN_OK;
@@ -138,11 +381,8 @@ hsgen_status solve_left_split(hsgen_ctx *ctx, int n, int nb, const double2 *U, d
 }  // namespace
 
 void reduce_release(hsgen_ctx *ctx) {
-  if (ctx->solver) cusolverDnDestroy((cusolverDnHandle_t)ctx->solver);
-  if (ctx->blas) cublasDestroy((cublasHandle_t)ctx->blas);
   if (ctx->ws_red.ptr) cudaFree(ctx->ws_red.ptr);
   if (ctx->h_info) cudaFreeHost(ctx->h_info);
-  ctx->solver = ctx->blas = nullptr;
   ctx->ws_red = Workspace{};
   ctx->h_info = nullptr;
 }
@@ -158,7 +398,7 @@ extern "C" hsgen_status hsgen_reduce_generalized(hsgen_ctx *ctx, int n, void *H,
   if (n == 0) return HSGEN_OK;
   if (!H || !S) return set_err(ctx, HSGEN_EINVAL, "reduce: NULL pointer");
   if (ld < n) return set_err(ctx, HSGEN_EINVAL, "reduce: ld < n");
-  if (ld > 0x7fffffffLL) return set_err(ctx, HSGEN_EINVAL, "reduce: ld above the 32-bit range of the solver");
+  if (ld > 0x7fffffffLL) return set_err(ctx, HSGEN_EINVAL, "reduce: ld above 2^31 - 1");
   if (H == S) return set_err(ctx, HSGEN_EINVAL, "reduce: H and S alias");
   HSG_CUDA(ctx, cudaSetDevice(ctx->device));
   if (!is_device_ptr(H) || !is_device_ptr(S))
@@ -168,100 +408,54 @@ extern "C" hsgen_status hsgen_reduce_generalized(hsgen_ctx *ctx, int n, void *H,
   hsgen_status pst = split_poll_status(ctx, false);  // an earlier build's expired wait
   if (pst != HSGEN_OK) return pst;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  if (!ctx->blas) {
-    cublasHandle_t h = nullptr;
-    cublasStatus_t e = cublasCreate(&h);
-    if (e != CUBLAS_STATUS_SUCCESS) return blas_err(ctx, (int)e, "cublasCreate");
-    ctx->blas = h;
-  }
-  if (!ctx->solver) {
-    cusolverDnHandle_t h = nullptr;
-    cusolverStatus_t e = cusolverDnCreate(&h);
-    if (e != CUSOLVER_STATUS_SUCCESS) return blas_err(ctx, (int)e, "cusolverDnCreate");
-    ctx->solver = h;
-  }
   if (!ctx->h_info) HSG_CUDA(ctx, cudaMallocHost(&ctx->h_info, sizeof(int)));
-  cublasHandle_t blas = (cublasHandle_t)ctx->blas;
-  cusolverDnHandle_t solver = (cusolverDnHandle_t)ctx->solver;
-  cublasStatus_t be = cublasSetStream(blas, s);
-  if (be != CUBLAS_STATUS_SUCCESS) return blas_err(ctx, (int)be, "cublasSetStream");
-  cusolverStatus_t se = cusolverDnSetStream(solver, s);
-  if (se != CUSOLVER_STATUS_SUCCESS) return blas_err(ctx, (int)se, "cusolverDnSetStream");
-
   const int uplo = ctx->opt.uplo;
-  const bool upper = uplo == 'U';
-  const cublasFillMode_t fill = upper ? CUBLAS_FILL_MODE_UPPER : CUBLAS_FILL_MODE_LOWER;
-  cuDoubleComplex *Sm = (cuDoubleComplex *)S, *Hm = (cuDoubleComplex *)H;
-  if (ctx->opt.precision == HSGEN_SPLIT && upper) {
-    // split form: S = U^H U blocked; Y = U^-H H; H~ = U^-H Y^H (= U^-H H U^-1, as H is Hermitian)
-    const int nb = reduce_block();
-    const int nblk = (n + nb - 1) / nb;
-    int lwork = 0;
-    se = cusolverDnZpotrf_bufferSize(solver, CUBLAS_FILL_MODE_UPPER, std::min(n, nb), Sm, (int)ld, &lwork);
-    if (se != CUSOLVER_STATUS_SUCCESS) return blas_err(ctx, (int)se, "cusolverDnZpotrf_bufferSize");
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t work_bytes = al(sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1));
-    const size_t info_bytes = al(sizeof(int) * (size_t)nblk);
-    const size_t gemm_bytes = split_gemm_ws_bytes(n, n, std::min(n, nb), kRedSlices);
-    hsgen_status st = ensure_ws(ctx, ctx->ws_red, work_bytes + info_bytes + gemm_bytes);
-    if (st != HSGEN_OK) return st;
-    char *base = (char *)ctx->ws_red.ptr;
-    cuDoubleComplex *work = (cuDoubleComplex *)base;
-    int *d_info = (int *)(base + work_bytes);
-    void *gws = base + work_bytes + info_bytes;
-    HSG_CUDA(ctx, cudaMemsetAsync(d_info, 0, sizeof(int) * nblk, s));
-    HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 0, s));
-    st = potrf_split(ctx, n, nb, (double2 *)S, ld, work, lwork, d_info, gws, s);
-    if (st == HSGEN_OK) st = solve_left_split(ctx, n, nb, (const double2 *)S, (double2 *)H, ld, gws, s);
-    if (st == HSGEN_OK) {
-      HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 2, s));
-      st = solve_left_split(ctx, n, nb, (const double2 *)S, (double2 *)H, ld, gws, s);
-    }
-    if (st == HSGEN_OK) HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 1, s));
-    HSG_CUDA(ctx, cudaStreamSynchronize(s));
-    if (st != HSGEN_OK) return st;
+  const bool lower = uplo != 'U';
+  const bool split = ctx->opt.precision == HSGEN_SPLIT;
+  const int nb = reduce_block();
+  if (split && !ctx->d_status) {
+    HSG_CUDA(ctx, cudaMalloc(&ctx->d_status, sizeof(int)));
+    HSG_CUDA(ctx, cudaMallocHost(&ctx->h_status, sizeof(int)));
+    HSG_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  }
+  hsgen_status st = ensure_ws(ctx, ctx->ws_red, red_layout(nullptr, n, ld, nb, split, lower).bytes);
+  if (st != HSGEN_OK) return st;
+  const RedWs w = red_layout(ctx->ws_red.ptr, n, ld, nb, split, lower);
+  ctx->launches = 0;
+  const int big = INT_MAX;
+  HSG_CUDA(ctx, cudaMemcpyAsync(w.info, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+  // S in the upper layout (the lower layout works on a conjugate-transposed copy)
+  double2 *Su = (double2 *)S;
+  if (lower) {
+    Su = w.Scopy;
+    const dim3 g((n + 31) / 32, (n + 7) / 8);
+    tri_transpose_kernel<<<g, dim3(32, 8), 0, s>>>(n, (const double2 *)S, Su, ld, 0);
+    HSG_LAUNCH(ctx, cudaGetLastError());
+  }
+  // S = U^H U; Y = U^-H H; H~ = U^-H Y^H (= U^-H H U^-1, as H is Hermitian)
+  HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 0, s));
+  st = potrf_blocked(ctx, split, n, nb, Su, ld, w, s);
+  if (st == HSGEN_OK) st = solve_left_blocked(ctx, split, n, nb, Su, (double2 *)H, ld, w, s);
+  if (st == HSGEN_OK) {
+    HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 2, s));
+    st = solve_left_blocked(ctx, split, n, nb, Su, (double2 *)H, ld, w, s);
+  }
+  if (st == HSGEN_OK) HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 1, s));
+  if (st == HSGEN_OK && lower) {  // L = U^H into S's lower triangle
+    const dim3 g((n + 31) / 32, (n + 7) / 8);
+    tri_transpose_kernel<<<g, dim3(32, 8), 0, s>>>(n, Su, (double2 *)S, ld, 1);
+    HSG_LAUNCH(ctx, cudaGetLastError());
+  }
+  HSG_CUDA(ctx, cudaMemcpyAsync(ctx->h_info, w.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HSG_CUDA(ctx, cudaStreamSynchronize(s));
+  if (st != HSGEN_OK) return st;
+  if (split) {
     st = split_check_status(ctx, s);
     if (st != HSGEN_OK) return st;
-    std::vector<int> info(nblk);
-    HSG_CUDA(ctx, cudaMemcpy(info.data(), d_info, sizeof(int) * nblk, cudaMemcpyDeviceToHost));
-    for (int b = 0; b < nblk; ++b) {
-      if (info[b] > 0)
-        return set_err(ctx, HSGEN_ENUMERIC, "reduce: S is not positive definite (leading minor " +
-                                                std::to_string(b * nb + info[b]) + ")");
-      if (info[b] < 0)
-        return set_err(ctx, HSGEN_ECUDA, "reduce: ZPOTRF argument " + std::to_string(-info[b]) + " invalid");
-    }
-    return HSGEN_OK;
   }
-  int lwork = 0;
-  se = cusolverDnZpotrf_bufferSize(solver, fill, n, Sm, (int)ld, &lwork);
-  if (se != CUSOLVER_STATUS_SUCCESS) return blas_err(ctx, (int)se, "cusolverDnZpotrf_bufferSize");
-  const size_t work_bytes = (sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1) + 255) / 256 * 256;
-  hsgen_status st = ensure_ws(ctx, ctx->ws_red, work_bytes + 256);
-  if (st != HSGEN_OK) return st;
-  cuDoubleComplex *work = (cuDoubleComplex *)ctx->ws_red.ptr;
-  int *d_info = (int *)((char *)ctx->ws_red.ptr + work_bytes);
-
-  // H in full (only its `uplo` triangle is read), then S = U^H U (or L L^H)
-  HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 0, s));
-  se = cusolverDnZpotrf(solver, fill, n, Sm, (int)ld, work, lwork, d_info);
-  if (se != CUSOLVER_STATUS_SUCCESS) return blas_err(ctx, (int)se, "cusolverDnZpotrf");
-  // 'U': H <- U^-H H, then H <- H U^-1;  'L': H <- L^-1 H, then H <- H L^-H
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0);
-  be = cublasZtrsm(blas, CUBLAS_SIDE_LEFT, fill, upper ? CUBLAS_OP_C : CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, n, &one,
-                   Sm, (int)ld, Hm, (int)ld);
-  if (be != CUBLAS_STATUS_SUCCESS) return blas_err(ctx, (int)be, "cublasZtrsm (left)");
-  be = cublasZtrsm(blas, CUBLAS_SIDE_RIGHT, fill, upper ? CUBLAS_OP_N : CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT, n, n,
-                   &one, Sm, (int)ld, Hm, (int)ld);
-  if (be != CUBLAS_STATUS_SUCCESS) return blas_err(ctx, (int)be, "cublasZtrsm (right)");
-  // exactly Hermitian: (H~ + H~^H) / 2
-  HSG_CUDA(ctx, launch_hermitian(n, (double2 *)H, ld, uplo, 1, s));
-  HSG_CUDA(ctx, cudaMemcpyAsync(ctx->h_info, d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HSG_CUDA(ctx, cudaStreamSynchronize(s));
   const int info = *ctx->h_info;
-  if (info > 0)
+  if (info != big)
     return set_err(ctx, HSGEN_ENUMERIC,
                    "reduce: S is not positive definite (leading minor " + std::to_string(info) + ")");
-  if (info < 0) return set_err(ctx, HSGEN_ECUDA, "reduce: ZPOTRF argument " + std::to_string(-info) + " invalid");
   return HSGEN_OK;
 }

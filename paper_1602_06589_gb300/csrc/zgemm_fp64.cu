@@ -199,6 +199,32 @@ __global__ void __launch_bounds__(NTHREADS) hs_kernel(int n_g, int depth, const 
   if (WITH_S) store_tile(S, ld, n_g, n_g, bi * MT, bj * NT, acc2, uplo, accumulate);
 }
 
+// General C (+)= (+-) P^H Q (P: K x M, Q: K x N, C: M x N): one CTA per
+// 64 x 64 tile (blockIdx.x row tile, blockIdx.y column tile); uplo 'U'
+// computes only the tiles and entries i <= j (diagonal imaginary parts 0).
+__global__ void __launch_bounds__(NTHREADS) gemm_kernel(int M, int N, int K, const double2 *__restrict__ P,
+                                                        long long ldp, const double2 *__restrict__ Q, long long ldq,
+                                                        double2 *__restrict__ C, long long ldc, int uplo,
+                                                        int accumulate, int negate) {
+  extern __shared__ double2 smem[];
+  const int i0 = blockIdx.x * MT, j0 = blockIdx.y * NT;
+  if (uplo == 'U' && i0 > j0 + NT - 1) return;
+  double acc[4][2][2][2], dummy[4][2][2][2];
+  zero_acc<false>(acc);
+  tile_mma<false>(P, ldp, Q, ldq, nullptr, M, N, K, i0, j0, acc, dummy, smem);
+  if (negate) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int d = 0; d < 2; ++d) acc[a][b][c][d] = -acc[a][b][c][d];
+  }
+  store_tile(C, ldc, M, N, i0, j0, acc, uplo, accumulate);
+}
+
 __global__ void mirror_kernel(int n, double2 *M, long long ld, int uplo) {
   int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -246,6 +272,21 @@ cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *
     hs_kernel<true><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate);
   else
     hs_kernel<false><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_fp64(int M, int N, int K, const double2 *P, long long ldp, const double2 *Q, long long ldq,
+                             double2 *C, long long ldc, int uplo, int accumulate, int negate, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  size_t sm = sizeof(double2) * 2 * 2 * KT * PADS;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((M + MT - 1) / MT, (N + NT - 1) / NT);
+  gemm_kernel<<<grid, NTHREADS, sm, s>>>(M, N, K, P, ldp, Q, ldq, C, ldc, uplo, accumulate, negate);
   return cudaGetLastError();
 }
 

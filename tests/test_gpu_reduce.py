@@ -1,7 +1,9 @@
 """GPU parity of the generalized-eigenproblem hand-off (Sec. 2.3, Eq.
 matrix_kohnsham) through the C ABI: S = U^H U (or L L^H) in place and
-H~ = U^-H H U^-1 in full; FP64 library form and the split form (blocked,
-updates as 7-slice BF16 products, to FP64-level accuracy).
+H~ = U^-H H U^-1 in full, blocked, in this library's kernels only: FP64
+tile kernels for the diagonal blocks (Cholesky and inverse), the products
+as FP64 DMMA (FP64 form) or 7-slice BF16 products (split form, to
+FP64-level accuracy).
 
 Inputs: the oracle's muffin-tin H, S plus a stand-in for the interstitial
 part (S + I, H + diag(|K_t|^2)) so that S is positive definite, uploaded in
@@ -58,9 +60,9 @@ def to_device(M, uplo):
                                                 ("FP64", "L", 600), ("SPLIT", "U", 90), ("SPLIT", "U", 600),
                                                 ("SPLIT", "U", 1300), ("SPLIT", "L", 600)])
 def test_reduce_matches_oracle(hs, precision, uplo, n_g):
-    """FP64: cuSOLVER / cuBLAS. SPLIT (upper triangle): blocks of 256, FP64
-    diagonal blocks, updates as 7-slice BF16 products on the tensor cores
-    (1, 3 and 6 blocks here); the lower triangle takes the FP64 path."""
+    """Blocks of 128 rows (1, 5 and 11 blocks here), diagonal blocks in FP64
+    tile kernels; products in FP64 DMMA (FP64) or as 7-slice BF16 products on
+    the tensor cores (SPLIT); the lower layout through a transposed copy."""
     import torch
 
     sysm, H, S = pd_problem(seed=3 + n_g, n_g=n_g)
