@@ -698,7 +698,7 @@ def main():
     peaks = _peaks()
 
     # dominant kernel: the H/S contraction
-    c_ms = statistics.mean(contract_ms)
+    c_ms = statistics.mean(contract_ms) or st["ms_total"]
     # with S in the Legendre form the contraction computes H only (half of F_HS),
     # over the rows l <= l_nonsph of each atom
     if st.get("s_form") == hsgen.S_LEGENDRE:

@@ -446,8 +446,15 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
   double2 *X = (double2 *)(ws + L.X);
   const bool split = ctx->opt.precision == HSGEN_SPLIT;
   auto chunks = atom_chunks(ctx);
-  const bool single = chunks.size() == 1;
-  const bool rec = record && single;
+  if (record) {
+    while (ctx->chunk_ev.size() < 5 * chunks.size()) {
+      cudaEvent_t e = nullptr;
+      HSG_CUDA(ctx, cudaEventCreate(&e));
+      ctx->chunk_ev.push_back(e);
+    }
+    ctx->chunks_timed = (int)chunks.size();
+  }
+  auto cev = [&](size_t ci, int k) { return ctx->chunk_ev[5 * ci + k]; };
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
   HSG_LAUNCH(ctx, launch_radial(n_g, job.kvec_dev, nt, ctx->d_radial, F, s));
   int slices = split ? choose_slices(ctx->opt.target_rel_err, ctx->opt.slices) : 0;
@@ -455,6 +462,7 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
     int a0 = chunks[ci].first, a1 = chunks[ci].second;
     int row_base = ctx->off[a0];
     int cdepth = ctx->off[a1] - row_base;
+    if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 0), s));
     for (int t = 0; t < nt; ++t) {
       // atoms of species t inside [a0, a1): contiguous range of the per-species list
       const auto &lst = ctx->atoms_of_type[t];
@@ -468,11 +476,12 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
                                           d_atoms, hi - lo, ctx->d_pos, ctx->d_rot, ctx->d_off, row_base,
                                           ctx->types[t].dpad, W, L.ldw, s));
     }
-    if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
+    if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 1), s));
     if (split) {
       const bool last = ci + 1 == chunks.size();
       hsgen_status st = split_chunk(ctx, n_g, a0, a1, W, X, L.ldw, job.H, job.leg ? nullptr : job.S, job.ld,
-                                    ci > 0, ws + L.split, slices, s, rec, last ? &job.copy : nullptr);
+                                    ci > 0, ws + L.split, slices, s, record ? &ctx->chunk_ev[5 * ci + 2] : nullptr,
+                                    last ? &job.copy : nullptr);
       if (st != HSGEN_OK) return st;
     } else {
       for (int t = 0; t < nt; ++t) {
@@ -486,11 +495,12 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
         HSG_LAUNCH(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].d_T, d_atoms,
                                            hi - lo, ctx->d_off, row_base, W, X, L.ldw, s));
       }
-      if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
-      if (rec) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
+      if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 2), s));
+      if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 3), s));
       HSG_LAUNCH(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H,
                                      job.leg ? nullptr : job.S, job.ld, ctx->opt.uplo, ci > 0 ? 1 : 0, s));
     }
+    if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 4), s));
   }
   if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
   if (job.leg) {
@@ -708,7 +718,7 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   }
   ctx->stats.kernel_launches = ctx->launches;
   ctx->stats.s_form = job.leg ? HSGEN_S_LEGENDRE : HSGEN_S_CONTRACTION;
-  ctx->phase_used[0] = atom_chunks(ctx).size() == 1;
+  ctx->phase_used[0] = 1;
   ctx->phase_used[1] = 1;
   ctx->phase_used[2] = job.leg != nullptr;
   ctx->phase_used[3] = host_io;
@@ -817,10 +827,15 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
     HSG_CUDA(ctx, cudaEventSynchronize(ctx->ev[5]));
     if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]) == cudaSuccess) st.ms_total = ms;
     if (ctx->phase_used[0]) {
-      if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st.ms_coefficients = ms;
-      if (cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) == cudaSuccess) st.ms_tapply = ms;
-      if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) == cudaSuccess) st.ms_slice = ms;
-      if (cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]) == cudaSuccess) st.ms_contract = ms;
+      // phases summed over the passes (the radial factors count as coefficients)
+      if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->chunk_ev[0]) == cudaSuccess) st.ms_coefficients = ms;
+      for (int ci = 0; ci < ctx->chunks_timed; ++ci) {
+        const cudaEvent_t *e = &ctx->chunk_ev[5 * ci];
+        if (cudaEventElapsedTime(&ms, e[0], e[1]) == cudaSuccess) st.ms_coefficients += ms;
+        if (cudaEventElapsedTime(&ms, e[1], e[2]) == cudaSuccess) st.ms_tapply += ms;
+        if (cudaEventElapsedTime(&ms, e[2], e[3]) == cudaSuccess) st.ms_slice += ms;
+        if (cudaEventElapsedTime(&ms, e[3], e[4]) == cudaSuccess) st.ms_contract += ms;
+      }
     }
     if (ctx->phase_used[2] && cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[6]) == cudaSuccess) st.ms_s = ms;
     if (ctx->phase_used[3]) {
@@ -860,6 +875,7 @@ void hsgen_destroy(hsgen_ctx *ctx) {
   reduce_release(ctx);
   if (ctx->events_ready)
     for (auto &e : ctx->ev) cudaEventDestroy(e);
+  for (auto &e : ctx->chunk_ev) cudaEventDestroy(e);
   delete ctx;
 }
 

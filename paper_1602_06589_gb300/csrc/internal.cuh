@@ -116,6 +116,10 @@ struct hsgen_ctx {
   // timing
   cudaEvent_t ev[10]{};
   bool events_ready = false;
+  // per pass over an atom chunk: start, coefficients done, X = T W done,
+  // slicing done, contraction done (5 events per chunk, created on demand)
+  std::vector<cudaEvent_t> chunk_ev;
+  int chunks_timed = 0;
   hsgen_stats stats{};
   long long launches = 0;           // kernels launched by the current call
   int phase_used[8]{};

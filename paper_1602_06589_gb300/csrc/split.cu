@@ -1847,7 +1847,7 @@ hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
 
 hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 *W, double2 *X, long long ldw,
                          double2 *H, double2 *S, long long ld, bool accumulate, void *ws, int slices,
-                         cudaStream_t s, bool record, const CopyOut *co) {
+                         cudaStream_t s, const cudaEvent_t *phase_ev, const CopyOut *co) {
   if (ctx->split_slices != slices) {
     hsgen_status st = split_prepare_types(ctx, slices);
     if (st != HSGEN_OK) return st;
@@ -1876,7 +1876,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
     hsgen_status st = tapply_split(ctx, n_g, a0, a1, Wsl, ldk, expW, X, ldw, slices, s);
     if (st != HSGEN_OK) return st;
   }
-  if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+  if (phase_ev) HSG_CUDA(ctx, cudaEventRecord(phase_ev[0], s));
   // (3) the operands of the contraction: X (right operand of H), W (left of
   // H, right of S) and U W (left of S), as residues or slices
   const CrtConsts cc = crt ? make_crt(pl.nmod) : CrtConsts{};
@@ -1892,7 +1892,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       HSG_LAUNCH(ctx, launch_slice(W, ldw, cdepth, ctx->d_urow + row_base, slices, 2, w.Ysl, ldk, plane, w.expY,
                                    n_g, s));
   }
-  if (record) HSG_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
+  if (phase_ev) HSG_CUDA(ctx, cudaEventRecord(phase_ev[1], s));
   // (4) H = W^H X and S = (U W)^H W over one triangle
   {
     const int bn = crt ? BNC : BN;

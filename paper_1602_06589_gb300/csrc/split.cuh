@@ -40,9 +40,10 @@ struct CopyOut {
 };
 // One pass (one chunk of atoms [a0, a1)) of the split path: slice W, X = T W,
 // slice X and U W, then one triangle of H (+)= W^H X and S (+)= (U W)^H W.
+// phase_ev (or null): two events, recorded after X = T W and after the slicing.
 hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 *W, double2 *X, long long ldw,
                          double2 *H, double2 *S, long long ld, bool accumulate, void *ws, int slices,
-                         cudaStream_t s, bool record, const CopyOut *co = nullptr);
+                         cudaStream_t s, const cudaEvent_t *phase_ev, const CopyOut *co = nullptr);
 // Makes `s` wait for the copies split_chunk queued on the copy stream.
 hsgen_status split_join_copies(hsgen_ctx *ctx, cudaStream_t s);
 // The device status word of the split launches (bounded waits): post queues
