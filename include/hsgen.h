@@ -154,6 +154,9 @@ typedef struct {
   int bits;                /* integer bits per operand (moduli scheme)          */
   int products;            /* BF16 products per FP64 product of the contraction */
   int atom_chunks;         /* passes over the atoms (a6) of the last build      */
+  double tuned_rel_err;    /* hsgen_autotune: relative Frobenius error of the   */
+                           /* chosen form against a 7-slice build (0: not       */
+                           /* measured)                                         */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -193,6 +196,22 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
  * earlier work has finished. */
 hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);
+
+/* Within one k-point, the part of hsgen_build_HS that one process of an
+ * nprow x npcol process grid owns in the 2-D block-cyclic layout of a
+ * distributed dense eigensolver (the paper's outlook, Sec. 5: distributed
+ * dense linear algebra): block (I, J) of block x block entries belongs to
+ * process (I mod nprow, J mod npcol). Writes exactly the entries of opt.uplo's
+ * triangle inside this process's (myrow, mycol) blocks of the full-size
+ * device buffers H and S (ld >= n_g) and leaves every other entry as it was;
+ * those entries are bit for bit the ones hsgen_build_HS writes, so the union
+ * over the grid is the whole build. Only the contraction's tiles are split
+ * (each process forms the coefficients of all plane waves, a few percent of
+ * the build). block: a multiple of 256. Device pointers only; not with
+ * opt.fill_full or S in the Legendre form (HSGEN_ENOTSUP). Asynchronous like
+ * hsgen_build_HS. */
+hsgen_status hsgen_build_HS_blocks(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
+                                   int block, int nprow, int npcol, int myrow, int mycol, void *cuda_stream);
 
 /* Builds H and S for n_k k-points in one go (one H, S per k-point, Sec. 2.3):
  * n_g[k], kvec[k] (host pointers to [n_g[k]][3]), H[k], S[k] device
@@ -238,13 +257,20 @@ hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T);
  * followed by zero rows up to offsets[a+1]. */
 hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
 
-/* Autotuner of the split form's schedule (no counterpart in the paper):
- * times hsgen_build_HS on this k-point for depth-segment lengths
- * {64, 96, 128, 192} blocks of 64 (tile band 16), then tile bands {8, 32}
- * with the best segment, keeps the fastest pair in the context for later
- * builds (batched ones included) and leaves H and S built with it. Same
- * arguments as hsgen_build_HS; synchronous; about eight builds long. The
- * FP64 form has nothing to tune: it builds once and returns HSGEN_OK. */
+/* Autotuner of the split form (no counterpart in the paper), on this
+ * k-point. (1) The form: with device outputs and neither a scheme nor a
+ * count forced in the options, it builds H and S once with 7 slices (~2e-15)
+ * as the reference, then measures the relative Frobenius error of candidate
+ * forms over the whole triangle: for each scheme (moduli 10..14, slices
+ * 5..7) the smallest count within half of opt.target_rel_err, searched from
+ * the a-priori choice; of the two, the faster build on this GPU is kept
+ * (hsgen_stats tuned_rel_err reports its error). (2) The schedule: times builds for
+ * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 (tile band 16),
+ * then tile bands {8, 32} with the best segment. The choices stay in the
+ * context for later builds (batched ones use the schedule) and H and S are
+ * left built with them. Same arguments as hsgen_build_HS; synchronous; about
+ * ten to fifteen builds long. The FP64 form has nothing to tune: it builds
+ * once and returns HSGEN_OK. */
 hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);
 

@@ -88,6 +88,48 @@ hsgen_status ensure_ws(hsgen_ctx *ctx, Workspace &w, size_t bytes) {
   return HSGEN_OK;
 }
 
+// Sums |A - B|^2 and |B|^2 over the uplo triangle (out[0], out[1]; atomics).
+__global__ void frob_diff_kernel(int n, const double2 *__restrict__ A, const double2 *__restrict__ B, long long ld,
+                                 int uplo, double *out) {
+  double d = 0.0, b = 0.0;
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    const int r0 = (uplo == 'U') ? 0 : j, r1 = (uplo == 'U') ? j + 1 : n;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double2 a = A[(size_t)j * ld + i], c = B[(size_t)j * ld + i];
+      const double x = a.x - c.x, y = a.y - c.y;
+      d += x * x + y * y;
+      b += c.x * c.x + c.y * c.y;
+    }
+  }
+  __shared__ double sd[32], sb[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sd[threadIdx.x >> 5] = d;
+    sb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double td = 0.0, tb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      td += sd[w];
+      tb += sb[w];
+    }
+    atomicAdd(out, td);
+    atomicAdd(out + 1, tb);
+  }
+}
+
+cudaError_t launch_frob_diff(int n, const double2 *A, const double2 *B, long long ld, int uplo, double *out,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  frob_diff_kernel<<<std::min(n, 4 * 152), 256, 0, s>>>(n, A, B, ld, uplo, out);
+  return cudaGetLastError();
+}
+
 static void free_system(hsgen_ctx *ctx) {
   for (auto &sp : ctx->types) {
     if (sp.d_T) cudaFree(sp.d_T);
@@ -498,7 +540,8 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
       if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 2), s));
       if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 3), s));
       HSG_LAUNCH(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H,
-                                     job.leg ? nullptr : job.S, job.ld, ctx->opt.uplo, ci > 0 ? 1 : 0, s));
+                                     job.leg ? nullptr : job.S, job.ld, ctx->opt.uplo, ci > 0 ? 1 : 0, ctx->owner,
+                                     s));
     }
     if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 4), s));
   }
@@ -725,6 +768,22 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   return HSGEN_OK;
 }
 
+hsgen_status hsgen_build_HS_blocks(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
+                                   int block, int nprow, int npcol, int myrow, int mycol, void *cuda_stream) {
+  if (!ctx) return HSGEN_EINVAL;
+  if (block <= 0 || block % 256 != 0 || nprow < 1 || npcol < 1 || myrow < 0 || myrow >= nprow || mycol < 0 ||
+      mycol >= npcol)
+    return set_err(ctx, HSGEN_EINVAL, "build_HS_blocks: bad block size (a multiple of 256) or process grid");
+  if (ctx->opt.fill_full || ctx->opt.s_form == HSGEN_S_LEGENDRE)
+    return set_err(ctx, HSGEN_ENOTSUP, "build_HS_blocks: not with fill_full or S in the Legendre form");
+  if (n_g > 0 && H && S && (!is_device_ptr(H) || !is_device_ptr(S)))
+    return set_err(ctx, HSGEN_EINVAL, "build_HS_blocks: H and S must be device pointers");
+  ctx->owner = BlockOwner{block, nprow, npcol, myrow, mycol};
+  const hsgen_status st = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+  ctx->owner = BlockOwner{};
+  return st;
+}
+
 hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec,
                                     void *const *H, void *const *S, const long long *ld, void *cuda_stream) {
   if (!ctx) return HSGEN_EINVAL;
@@ -767,9 +826,146 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
                             void *cuda_stream) {
   if (!ctx) return HSGEN_EINVAL;
   if (ctx->opt.precision != HSGEN_SPLIT) return hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+  if (n_g <= 0 || !H || !S || ld < n_g) return hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  // one timed build per candidate (device time of the whole build); the
-  // first is preceded by an untimed build that sets up the workspaces
+  HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+  ctx->stats.tuned_rel_err = 0.0;
+  // (1) the split form's scheme and count, from the error measured on this
+  // k-point: each candidate's H and S against a 7-slice build (~2e-15), over
+  // the whole triangle; the cheapest candidate within half the target wins.
+  // Only with device outputs and when the caller forced neither a scheme nor
+  // a count.
+  const bool dev = is_device_ptr(H) && is_device_ptr(S);
+  if (dev && ctx->opt.scheme == HSGEN_SCHEME_AUTO && ctx->opt.slices == 0 && ctx->opt.moduli == 0) {
+    const hsgen_options saved = ctx->opt;
+    auto set_form = [&](int scheme, int count) {
+      ctx->opt.scheme = scheme;
+      ctx->opt.slices = scheme == HSGEN_SCHEME_SLICES ? count : 0;
+      ctx->opt.moduli = scheme == HSGEN_SCHEME_MODULI ? count : 0;
+    };
+    const size_t bytes = sizeof(double2) * (size_t)ld * n_g;
+    hsgen_status st = ensure_ws(ctx, ctx->ws_ref, 2 * bytes + 256);
+    if (st != HSGEN_OK) return st;
+    double2 *Hr = (double2 *)ctx->ws_ref.ptr, *Sr = (double2 *)((char *)ctx->ws_ref.ptr + bytes);
+    double *acc = (double *)((char *)ctx->ws_ref.ptr + 2 * bytes);
+    set_form(HSGEN_SCHEME_SLICES, kMaxSlices);
+    st = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+    if (st != HSGEN_OK) {
+      ctx->opt = saved;
+      return st;
+    }
+    HSG_CUDA(ctx, cudaMemcpyAsync(Hr, H, bytes, cudaMemcpyDeviceToDevice, s));
+    HSG_CUDA(ctx, cudaMemcpyAsync(Sr, S, bytes, cudaMemcpyDeviceToDevice, s));
+    auto measure = [&](int scheme, int count, double &err) -> hsgen_status {
+      set_form(scheme, count);
+      hsgen_status st2 = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+      if (st2 != HSGEN_OK) return st2;
+      double h[4];
+      HSG_CUDA(ctx, cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
+      HSG_CUDA(ctx, launch_frob_diff(n_g, (const double2 *)H, Hr, ld, ctx->opt.uplo, acc, s));
+      HSG_CUDA(ctx, launch_frob_diff(n_g, (const double2 *)S, Sr, ld, ctx->opt.uplo, acc + 2, s));
+      HSG_CUDA(ctx, cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+      HSG_CUDA(ctx, cudaStreamSynchronize(s));
+      st2 = split_poll_status(ctx, true);
+      if (st2 != HSGEN_OK) return st2;
+      err = std::max(std::sqrt(h[0] / std::max(h[1], 1e-300)), std::sqrt(h[2] / std::max(h[3], 1e-300)));
+      return HSGEN_OK;
+    };
+    // candidates by BF16 products per FP64 product: moduli 10..14, then slices 5, 6, 7
+    std::vector<std::pair<int, int>> cand;
+    for (int n = kMinModuli; n <= 14; ++n) cand.push_back({HSGEN_SCHEME_MODULI, n});
+    for (int sl = 5; sl <= kMaxSlices; ++sl) cand.push_back({HSGEN_SCHEME_SLICES, sl});
+    // start at the a-priori choice, then walk down while the measured error
+    // allows it, or up while it does not
+    int depth = 0;
+    for (auto c : atom_chunks(ctx)) depth = std::max(depth, ctx->off[c.second] - ctx->off[c.first]);
+    const double target = saved.target_rel_err, accept = 0.5 * target;
+    int k0 = (int)cand.size() - 1;
+    const int n0 = choose_moduli(target, 0, depth);
+    if (n0 > 0) {
+      k0 = n0 - kMinModuli;
+    } else {
+      for (int k = 14 - kMinModuli + 1; k < (int)cand.size(); ++k)
+        if (cand[k].second >= choose_slices(target, 0)) {
+          k0 = k;
+          break;
+        }
+    }
+    std::vector<double> errs(cand.size(), -1.0);
+    auto err_of = [&](int k, double &e) -> hsgen_status {
+      if (errs[k] < 0.0) {
+        hsgen_status st2 = measure(cand[k].first, cand[k].second, errs[k]);
+        if (st2 != HSGEN_OK) return st2;
+      }
+      e = errs[k];
+      return HSGEN_OK;
+    };
+    // the cheapest accurate count of each scheme (moduli: candidates
+    // [0, nm), slices: [nm, size)); the error falls with the count
+    const int nm = 14 - kMinModuli + 1;
+    auto cheapest = [&](int lo, int hi, int start, int &chosen) -> hsgen_status {
+      chosen = -1;
+      double e = 0.0;
+      start = std::max(lo, std::min(hi - 1, start));
+      hsgen_status st2 = err_of(start, e);
+      if (st2 != HSGEN_OK) return st2;
+      if (e <= accept) {
+        chosen = start;
+        for (int k = start - 1; k >= lo; --k) {
+          st2 = err_of(k, e);
+          if (st2 != HSGEN_OK) return st2;
+          if (e > accept) break;
+          chosen = k;
+        }
+      } else {
+        for (int k = start + 1; k < hi; ++k) {
+          st2 = err_of(k, e);
+          if (st2 != HSGEN_OK) return st2;
+          if (e <= accept) {
+            chosen = k;
+            break;
+          }
+        }
+      }
+      return HSGEN_OK;
+    };
+    int cm = -1, cs = -1;
+    st = cheapest(0, nm, k0 < nm ? k0 : nm - 1, cm);
+    if (st == HSGEN_OK) st = cheapest(nm, (int)cand.size(), k0 >= nm ? k0 : nm + 1, cs);
+    // both schemes accurate: the faster one on this GPU (BF16 products per
+    // FP64 product decide only at equal energy per product; the tensor
+    // cores run under the power cap)
+    int chosen = cm >= 0 ? cm : cs;
+    if (st == HSGEN_OK && cm >= 0 && cs >= 0) {
+      double t[2] = {0.0, 0.0};
+      const int ks[2] = {cm, cs};
+      for (int r = 0; r < 2 && st == HSGEN_OK; ++r) {
+        set_form(cand[ks[r]].first, cand[ks[r]].second);
+        for (int rep = 0; rep < 2 && st == HSGEN_OK; ++rep) {  // the second build is timed
+          st = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+          if (st == HSGEN_OK) st = split_poll_status(ctx, true);
+        }
+        float ms = 0.f;
+        if (st == HSGEN_OK && cudaEventSynchronize(ctx->ev[5]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]) == cudaSuccess)
+          t[r] = ms;
+      }
+      chosen = (t[1] > 0.0 && t[1] < t[0]) ? cs : cm;
+    }
+    cudaFree(ctx->ws_ref.ptr);
+    ctx->ws_ref = Workspace{};
+    if (st != HSGEN_OK) {
+      ctx->opt = saved;
+      return st;
+    }
+    if (chosen < 0) chosen = (int)cand.size() - 1;  // nothing meets the target: the most accurate form
+    ctx->opt = saved;
+    set_form(cand[chosen].first, cand[chosen].second);
+    ctx->stats.tuned_rel_err = errs[chosen] >= 0.0 ? errs[chosen] : 0.0;
+  }
+  // (2) the schedule: one timed build per candidate (device time of the
+  // whole build); the first is preceded by an untimed build that sets up the
+  // workspaces
   bool warm = false;
   auto trial = [&](int kseg, int band, double &ms) -> hsgen_status {
     ctx->kseg_blocks = kseg;
@@ -792,7 +988,7 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   };
   int best_k = ctx->kseg_blocks, best_b = ctx->tile_band;
   double best = 1e300;
-  for (int kseg : {128, 64, 96, 192}) {
+  for (int kseg : {128, 64, 96, 192, 256}) {
     double ms = 0.0;
     hsgen_status st = trial(kseg, 16, ms);
     if (st != HSGEN_OK) return st;
@@ -813,7 +1009,10 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   }
   ctx->kseg_blocks = best_k;
   ctx->tile_band = best_b;
-  return hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+  const double tuned = ctx->stats.tuned_rel_err;
+  hsgen_status st = hsgen_build_HS(ctx, n_g, kvec, H, S, ld, cuda_stream);
+  ctx->stats.tuned_rel_err = tuned;
+  return st;
 }
 
 hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
@@ -872,6 +1071,7 @@ void hsgen_destroy(hsgen_ctx *ctx) {
   if (ctx->ws_main.ptr) cudaFree(ctx->ws_main.ptr);
   if (ctx->ws_out.ptr) cudaFree(ctx->ws_out.ptr);
   if (ctx->ws_leg.ptr) cudaFree(ctx->ws_leg.ptr);
+  if (ctx->ws_ref.ptr) cudaFree(ctx->ws_ref.ptr);
   reduce_release(ctx);
   if (ctx->events_ready)
     for (auto &e : ctx->ev) cudaEventDestroy(e);

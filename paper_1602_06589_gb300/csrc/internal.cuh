@@ -60,6 +60,19 @@ struct Workspace {
 // b-bit integer operands). `slices` is also the slice count of T and of
 // X = T W in either form.
 enum { kSchemeSlices = 1, kSchemeModuli = 2 };
+
+// 2-D block-cyclic ownership of H and S blocks (block x block entries) over
+// an nprow x npcol process grid: this process (myrow, mycol) owns block
+// (I, J) when I % nprow == myrow and J % npcol == mycol. block = 0: all.
+struct BlockOwner {
+  int block = 0, nprow = 1, npcol = 1, myrow = 0, mycol = 0;
+  __host__ __device__ bool owns(long long row, long long col) const {
+    return block == 0 || ((row / block) % nprow == myrow && (col / block) % npcol == mycol);
+  }
+  bool operator==(const BlockOwner &o) const {
+    return block == o.block && nprow == o.nprow && npcol == o.npcol && myrow == o.myrow && mycol == o.mycol;
+  }
+};
 struct SplitPlan {
   int scheme = kSchemeSlices;
   int slices = 0, nmod = 0, bits = 0;
@@ -90,6 +103,7 @@ struct hsgen_ctx {
   hsg::Workspace ws_main;           // W, X, radial factors, kvec copy, split slices
   hsg::Workspace ws_out;            // device H/S staging when the caller passes host pointers
   hsg::Workspace ws_leg;            // S in the Legendre form: coordinates, structure factors, tables
+  hsg::Workspace ws_ref;            // autotuner: the reference H and S it measures errors against
   hsg::Workspace ws_red;            // generalized-eigenproblem reduction: block inverses, products, status
   int *h_info = nullptr;            // pinned host copy of the factorization status
   int split_slices = 0;             // slices the species' T were cut into
@@ -105,6 +119,8 @@ struct hsgen_ctx {
   int tiles_band = 0;               // band the cached tile list was built with
   int tiles_bn = 0;                 // tile width (complex columns) of that list
   hsg::SplitPlan last_plan;         // split form of the last pass
+  hsg::BlockOwner owner;            // blocks of H and S the current build writes
+  hsg::BlockOwner tiles_owner;      // ownership the cached tile list was built for
   int auto_chunk = 0;               // atoms per pass chosen by the library (0: all), see atom_chunk
   std::vector<int2> tiles_host;     // host copy of that list (column bands of the overlapped copies)
   cudaStream_t copy_stream = nullptr;  // host outputs: copies of finished column bands
@@ -198,7 +214,7 @@ cudaError_t launch_tapply_fp64(int dpad, int n_g, const double2 *T, const int *a
 // a4: upper (or lower) triangle of H += W^H X and S += W^H diag(u) W (FP64 DMMA).
 cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *X, const double *urow,
                            long long ldw, double2 *H, double2 *S, long long ld, int uplo, int accumulate,
-                           cudaStream_t s);
+                           const BlockOwner &own, cudaStream_t s);
 // C (+)= (+-) P^H Q in FP64 (DMMA): P is K x M, Q is K x N (complex, column-major), C is M x N;
 // uplo 'U': only the entries i <= j (diagonal imaginary parts set to 0); C must not overlap P or Q.
 cudaError_t launch_gemm_fp64(int M, int N, int K, const double2 *P, long long ldp, const double2 *Q, long long ldq,

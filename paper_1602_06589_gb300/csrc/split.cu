@@ -1144,9 +1144,11 @@ __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ 
 // Moduli form: residues of the b-bit integers N = round(v 2^(b - e)) (one
 // scale 2^e per column) for every modulus, balanced to |r| <= 128, as BF16
 // planes in the k-blocked layout of slice_kernel; plane i * planes + {0, 1, 2}
-// holds re, im, -re of modulus i. N mod m is formed from N's base-256 digits
-// and the table 256^j mod m, so no 64-bit division is needed.
-__constant__ int c_pow256[kMaxModuli][6];
+// holds re, im, -re of modulus i. |N| < 2^48 is cut into three 16-bit pieces,
+// so |N| mod m = (p2 (2^32 mod m) + p1 (2^16 mod m) + p0) mod m with 32-bit
+// integer arithmetic only. Each thread takes two consecutive depth rows (one
+// 4-byte store per plane).
+__constant__ int c_pow16[kMaxModuli][2];  // 2^16 mod m_i, 2^32 mod m_i
 
 __global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict__ src, long long lds, int K,
                                                       const double *__restrict__ urow, int b, CrtConsts crt,
@@ -1175,44 +1177,48 @@ __global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict_
   }
   __syncthreads();
   const int shift = b - e_sh;
-  for (int k = threadIdx.x; k < (int)ldk; k += blockDim.x) {
-    __nv_bfloat16 *out = dst + ((size_t)(k >> 6) * ncols + col) * 64 + (k & 63);
-    long long N[2] = {0, 0};
-    if (k < K) {
-      double2 v = c[k];
-      if (urow) {
-        const double u = urow[k];
-        v.x *= u;
-        v.y *= u;
+  for (int k = 2 * threadIdx.x; k < (int)ldk; k += 2 * blockDim.x) {  // ldk is a multiple of 64
+    // (row, re/im): magnitude pieces and sign
+    int p0[4], p1[4], p2[4];
+    bool ng[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      long long N[2] = {0, 0};
+      if (k + h < K) {
+        double2 v = c[k + h];
+        if (urow) {
+          const double u = urow[k + h];
+          v.x *= u;
+          v.y *= u;
+        }
+        N[0] = to_fixed(v.x, shift);
+        N[1] = to_fixed(v.y, shift);
       }
-      N[0] = to_fixed(v.x, shift);
-      N[1] = to_fixed(v.y, shift);
-    }
-    int dg[2][6];
-    bool ng[2];
-#pragma unroll
-    for (int z = 0; z < 2; ++z) {
-      ng[z] = N[z] < 0;
-      const unsigned long long a = ng[z] ? (unsigned long long)(-N[z]) : (unsigned long long)N[z];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) dg[z][j] = (int)((a >> (8 * j)) & 0xFFu);
-    }
-    for (int i = 0; i < crt.n; ++i) {
-      const int m = crt.m[i];
-      int r[2];
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
-        int acc = 0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) acc += dg[z][j] * c_pow256[i][j];
-        int x = mod_small(acc, m, crt.inv_m[i]);  // |N| mod m
-        if (ng[z] && x) x = m - x;                // N mod m
-        r[z] = (2 * x > m) ? x - m : x;           // balanced: |r| <= m / 2 <= 128
+        const int q = 2 * z + h;
+        ng[q] = N[z] < 0;
+        const unsigned long long a = ng[q] ? (unsigned long long)(-N[z]) : (unsigned long long)N[z];
+        p0[q] = (int)(a & 0xFFFFu);
+        p1[q] = (int)((a >> 16) & 0xFFFFu);
+        p2[q] = (int)(a >> 32);
       }
-      __nv_bfloat16 *base = out + (size_t)i * planes * plane_stride;
-      base[0] = __float2bfloat16_rn((float)r[0]);
-      base[plane_stride] = __float2bfloat16_rn((float)r[1]);
-      if (planes == 3) base[2 * plane_stride] = __float2bfloat16_rn((float)-r[0]);
+    }
+    __nv_bfloat16 *out = dst + ((size_t)(k >> 6) * ncols + col) * 64 + (k & 63);
+    for (int i = 0; i < crt.n; ++i) {
+      const int m = crt.m[i];
+      const int c16 = c_pow16[i][0], c32 = c_pow16[i][1];
+      float r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int x = mod_small(p2[q] * c32 + p1[q] * c16 + p0[q], m, crt.inv_m[i]);  // |N| mod m (< 2^25 in)
+        if (ng[q] && x) x = m - x;                                              // N mod m
+        r[q] = (float)((2 * x > m) ? x - m : x);                                // balanced, |r| <= 128
+      }
+      __nv_bfloat162 *base = (__nv_bfloat162 *)(out + (size_t)i * planes * plane_stride);
+      base[0] = __floats2bfloat162_rn(r[0], r[1]);  // re of rows k, k + 1
+      *(__nv_bfloat162 *)((__nv_bfloat16 *)base + plane_stride) = __floats2bfloat162_rn(r[2], r[3]);
+      if (planes == 3) *(__nv_bfloat162 *)((__nv_bfloat16 *)base + 2 * plane_stride) = __floats2bfloat162_rn(-r[0], -r[1]);
     }
   }
 }
@@ -1390,17 +1396,15 @@ CrtConsts make_crt(int n) {
   return c;
 }
 
-// 256^j mod m_i for the residue kernel (constant memory, once per device)
+// 2^16 and 2^32 mod m_i for the residue kernel (constant memory, once per device)
 cudaError_t upload_crt_table() {
-  int tab[kMaxModuli][6];
+  int tab[kMaxModuli][2];
   for (int i = 0; i < kMaxModuli; ++i) {
-    long long p = 1;
-    for (int j = 0; j < 6; ++j) {
-      tab[i][j] = (int)p;
-      p = (p * 256) % kModuli[i];
-    }
+    const long long m = kModuli[i];
+    tab[i][0] = (int)((1LL << 16) % m);
+    tab[i][1] = (int)((1LL << 32) % m);
   }
-  return cudaMemcpyToSymbol(c_pow256, tab, sizeof(tab));
+  return cudaMemcpyToSymbol(c_pow16, tab, sizeof(tab));
 }
 
 cudaError_t launch_slice(const double2 *src, long long lds, int K, const double *urow, int s, int planes,
@@ -1898,8 +1902,15 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
     const int bn = crt ? BNC : BN;
     // tiles in bands of tile_band 64-column blocks (the same width in columns for either tile)
     const int band = crt ? std::max(1, ctx->tile_band * BN / BNC) : ctx->tile_band;
-    if (ctx->tiles_n != n_g || ctx->tiles_uplo != uplo || ctx->tiles_band != band || ctx->tiles_bn != bn) {
+    if (ctx->tiles_n != n_g || ctx->tiles_uplo != uplo || ctx->tiles_band != band || ctx->tiles_bn != bn ||
+        !(ctx->tiles_owner == ctx->owner)) {
       std::vector<int2> tl = tri_tiles(n_g, uplo, band, bn);
+      if (ctx->owner.block) {  // only the tiles of this process's blocks (a tile lies inside one block)
+        std::vector<int2> mine;
+        for (const int2 &t : tl)
+          if (ctx->owner.owns((long long)t.x * BMT, (long long)t.y * bn)) mine.push_back(t);
+        tl.swap(mine);
+      }
       if (ctx->d_tiles) cudaFree(ctx->d_tiles);
       ctx->d_tiles = nullptr;
       ctx->tiles_n = -1;
@@ -1910,8 +1921,10 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       ctx->tiles_uplo = uplo;
       ctx->tiles_band = band;
       ctx->tiles_bn = bn;
+      ctx->tiles_owner = ctx->owner;
       ctx->tiles_count = (long long)tl.size();
     }
+    if (ctx->tiles_count == 0) return HSGEN_OK;
     const int nkb_all = (int)(ldk / BK);
     // moduli form: at most 256 k-blocks per launch (32 chunks of exact FP32
     // sums keep the epilogue's int32 sums below 2^29)

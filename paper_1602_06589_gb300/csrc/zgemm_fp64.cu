@@ -183,7 +183,7 @@ template <bool WITH_S>
 __global__ void __launch_bounds__(NTHREADS) hs_kernel(int n_g, int depth, const double2 *__restrict__ W,
                                                       const double2 *__restrict__ X, const double *__restrict__ urow,
                                                       long long ldw, double2 *__restrict__ H, double2 *__restrict__ S,
-                                                      long long ld, int uplo, int accumulate) {
+                                                      long long ld, int uplo, int accumulate, BlockOwner own) {
   extern __shared__ double2 smem[];
   long long x = blockIdx.x;
   int hi = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(NTHREADS) hs_kernel(int n_g, int depth, const 
   while ((long long)(hi + 1) * (hi + 2) / 2 <= x) ++hi;
   int lo = (int)(x - (long long)hi * (hi + 1) / 2);  // lo <= hi
   int bi = (uplo == 'U') ? lo : hi, bj = (uplo == 'U') ? hi : lo;
+  if (!own.owns((long long)bi * MT, (long long)bj * NT)) return;  // 64 x 64 tiles lie inside one block
   double acc1[4][2][2][2], acc2[4][2][2][2];
   zero_acc<true>(acc1);
   zero_acc<WITH_S>(acc2);
@@ -254,7 +255,8 @@ cudaError_t launch_tapply_fp64(int dpad, int n_g, const double2 *T, const int *a
 }
 
 cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *X, const double *urow, long long ldw,
-                           double2 *H, double2 *S, long long ld, int uplo, int accumulate, cudaStream_t s) {
+                           double2 *H, double2 *S, long long ld, int uplo, int accumulate, const BlockOwner &own,
+                           cudaStream_t s) {
   if (n_g <= 0) return cudaSuccess;
   size_t sm = sizeof(double2) * 2 * 3 * KT * PADS;
   static bool attr = false;
@@ -269,9 +271,11 @@ cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *
   long long ntiles = nb * (nb + 1) / 2;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (S)
-    hs_kernel<true><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate);
+    hs_kernel<true><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate,
+                                                           own);
   else
-    hs_kernel<false><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate);
+    hs_kernel<false><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate,
+                                                            own);
   return cudaGetLastError();
 }
 

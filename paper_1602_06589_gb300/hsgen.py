@@ -50,10 +50,11 @@ class Stats(C.Structure):
                 ("workspace_bytes", C.c_longlong), ("kernel_launches", C.c_longlong), ("s_form", C.c_int),
                 ("ms_s", C.c_double), ("kseg_blocks", C.c_int), ("tile_band", C.c_int),
                 ("ms_upload", C.c_double), ("ms_download", C.c_double), ("scheme", C.c_int), ("moduli", C.c_int),
-                ("bits", C.c_int), ("products", C.c_int), ("atom_chunks", C.c_int)]
+                ("bits", C.c_int), ("products", C.c_int), ("atom_chunks", C.c_int), ("tuned_rel_err", C.c_double)]
 
 
-EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_batched",
+EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_blocks",
+           "hsgen_build_HS_batched",
            "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_autotune",
            "hsgen_reduce_generalized", "hsgen_get_stats", "hsgen_synchronize", "hsgen_last_error",
            "hsgen_destroy"]
@@ -84,6 +85,8 @@ def load(path: Optional[str] = None):
         lib.hsgen_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Options)]
         lib.hsgen_set_atoms.argtypes = [vp, _dp, C.c_double, C.c_int, C.POINTER(TypeDesc), C.c_int, _ip, _dp, _dp]
         lib.hsgen_build_HS.argtypes = [vp, C.c_int, vp, vp, vp, C.c_longlong, vp]
+        lib.hsgen_build_HS_blocks.argtypes = [vp, C.c_int, vp, vp, vp, C.c_longlong, C.c_int, C.c_int, C.c_int,
+                                              C.c_int, C.c_int, vp]
         lib.hsgen_build_HS_batched.argtypes = [vp, C.c_int, _ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                                C.POINTER(C.c_longlong), vp]
         lib.hsgen_coefficients.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
@@ -174,6 +177,14 @@ def hsgen_build_HS(ctx, n_g: int, kvec_ptr: int, H_ptr: int, S_ptr: int, ld: int
     st = load().hsgen_build_HS(ctx, int(n_g), C.c_void_p(kvec_ptr), C.c_void_p(H_ptr), C.c_void_p(S_ptr),
                                int(ld), C.c_void_p(stream))
     _check(ctx, st, "hsgen_build_HS")
+
+
+def hsgen_build_HS_blocks(ctx, n_g: int, kvec_ptr: int, H_ptr: int, S_ptr: int, ld: int, block: int, nprow: int,
+                          npcol: int, myrow: int, mycol: int, stream: int = 0):
+    st = load().hsgen_build_HS_blocks(ctx, int(n_g), C.c_void_p(kvec_ptr), C.c_void_p(H_ptr), C.c_void_p(S_ptr),
+                                      int(ld), int(block), int(nprow), int(npcol), int(myrow), int(mycol),
+                                      C.c_void_p(stream))
+    _check(ctx, st, "hsgen_build_HS_blocks")
 
 
 def hsgen_build_HS_batched(ctx, n_g: Sequence[int], kvec_ptrs, H_ptrs, S_ptrs, lds, stream: int = 0):

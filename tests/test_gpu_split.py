@@ -316,12 +316,43 @@ def test_split_autotune_choice_and_parity(hs):
         H, S = g.autotune(kd)
         torch.cuda.synchronize()
         st = g.stats()
-        assert st["kseg_blocks"] in (64, 96, 128, 192) and st["tile_band"] in (8, 16, 32)
+        assert st["kseg_blocks"] in (64, 96, 128, 192, 256) and st["tile_band"] in (8, 16, 32)
         H2, S2 = g.build(kd)
         torch.cuda.synchronize()
         assert torch.equal(H, H2) and torch.equal(S, S2)
         assert g.stats()["kseg_blocks"] == st["kseg_blocks"]
     check(w.system, kv, H.cpu().numpy(), S.cpu().numpy())
+
+
+@pytest.mark.parametrize("target", [1e-11, 1e-14])
+def test_autotune_picks_the_form_by_measured_error(hs, target):
+    """The autotuner measures candidate forms against a 7-slice build over
+    the whole triangle, takes each scheme's smallest count within half the
+    target and keeps the faster of the two; only 7 slices reach 1e-14 (the
+    moduli form stops near 1e-13, where X = T W's own rounding lies)."""
+    import torch
+
+    w = make_config(2, n_g_override=1200)
+    kd = torch.from_numpy(w.kvecs[0]).cuda()
+    with hs.Generator(w.system, precision=hs.SPLIT, target_rel_err=target) as g:
+        H, S = g.autotune(kd)
+        g.synchronize()
+        st = g.stats()
+        H2, S2 = g.build(kd)  # the choice stays in the context
+        g.synchronize()
+        assert torch.equal(H, H2) and torch.equal(S, S2)
+        st2 = g.stats()
+    assert st2["scheme"] == st["scheme"] and st2["products"] == st["products"]
+    # (7 slices are the reference itself: measured 0)
+    assert 0.0 <= st["tuned_rel_err"] <= 0.5 * target and (st["tuned_rel_err"] > 0.0) == (target == 1e-11)
+    if target == 1e-11:
+        assert (st["scheme"] == hs.SCHEME_MODULI and st["products"] <= 13) or \
+            (st["scheme"] == hs.SCHEME_SLICES and st["slices"] <= 6)
+    else:
+        assert st["scheme"] == hs.SCHEME_SLICES and st["slices"] == 7
+    # the measured figure is the real error (to the reference's ~1e-15)
+    (hf, _), (sf, _), _ = errors(w.system, w.kvecs[0], H.cpu().numpy(), S.cpu().numpy())
+    assert max(hf, sf) <= max(2.0 * st["tuned_rel_err"], 1e-14)
 
 
 def test_split_timeout_is_reported_and_context_recovers(hs):

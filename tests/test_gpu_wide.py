@@ -176,3 +176,50 @@ def test_fp64_config4_columns(hs, config4_columns):
     w, Ho, So, norms = config4_columns
     Hc, Sc = library_columns(hs, w, "fp64")
     check_columns(Hc, Sc, Ho, So, norms, REL["fp64"])
+
+
+@pytest.mark.parametrize("form,scheme", [("split", "moduli"), ("split", "slices"), ("fp64", None)])
+@pytest.mark.parametrize("grid", [(2, 1), (2, 2), (1, 3)])
+def test_block_cyclic_parts_make_the_whole_build(hs, form, scheme, grid):
+    """hsgen_build_HS_blocks: each process of the grid writes exactly its
+    2-D block-cyclic blocks of the triangle, bit for bit the entries of the
+    whole build; the union over the grid is the whole build (64 atoms, N_G
+    1500: 6 x 6 blocks of 256)."""
+    import torch
+
+    from paper_1602_06589_gb300 import partition
+
+    w = make_config(2, n_g_override=1500)
+    kv = torch.from_numpy(w.kvecs[0]).cuda()
+    n = kv.shape[0]
+    kw = {"precision": hs.SPLIT if form == "split" else hs.FP64}
+    if scheme:
+        kw["scheme"] = hs.SCHEME_MODULI if scheme == "moduli" else hs.SCHEME_SLICES
+    nprow, npcol = grid
+    block = 256
+    with hs.Generator(w.system, **kw) as g:
+        Hf, Sf = g.build(kv)
+        g.synchronize()
+        Hf, Sf = Hf.cpu().numpy(), Sf.cpu().numpy()
+        union = np.zeros((n, n), bool)
+        for rank in range(nprow * npcol):
+            myrow, mycol = divmod(rank, npcol)
+            sentinel = complex(3.0, -3.0)
+            Hb = torch.full((n, n), sentinel, dtype=torch.complex128, device="cuda")
+            Sb = torch.full_like(Hb, sentinel)
+            hs.hsgen_build_HS_blocks(g.ctx, n, kv.data_ptr(), Hb.data_ptr(), Sb.data_ptr(), n, block, nprow, npcol,
+                                     myrow, mycol, 0)
+            g.synchronize()
+            Hb, Sb = Hb.mT.cpu().numpy(), Sb.mT.cpu().numpy()  # matrix views of the column-major buffers
+            i, j = np.indices((n, n))
+            mine = (i <= j) & ((i // block) % nprow == myrow) & ((j // block) % npcol == mycol)
+            assert np.array_equal(Hb[mine], Hf[mine]) and np.array_equal(Sb[mine], Sf[mine])
+            assert np.all(Hb[~mine] == sentinel) and np.all(Sb[~mine] == sentinel)
+            # the same blocks by the host-side partition helper (square blocks, most square grid)
+            if (nprow, npcol) == partition.grid_shape(nprow * npcol):
+                tiles = set(partition.tiles_of_rank(n, block, rank, nprow * npcol))
+                assert tiles == {(bi, bj) for bi in range(6) for bj in range(6)
+                                 if bi <= bj and bi % nprow == myrow and bj % npcol == mycol}
+            assert not np.any(union & mine)
+            union |= mine
+        assert np.array_equal(union, np.triu(np.ones((n, n), bool)))
