@@ -1296,13 +1296,23 @@ int max_pairs() {
   return n;
 }
 
-cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
+// Shared-memory attribute of both tensor-core kernels (once per process; set
+// before any stream capture).
+cudaError_t gemm_attrs() {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(crt_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
+  cudaError_t e = gemm_attrs();
+  if (e != cudaSuccess) return e;
   if (P.ntiles <= 0) return cudaSuccess;
   const long long pairs = std::min<long long>(P.ntiles, max_pairs());
   split_gemm_kernel<<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
@@ -1310,12 +1320,8 @@ cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
 }
 
 cudaError_t launch_crt(GemmParams &P, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(crt_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = gemm_attrs();
+  if (e != cudaSuccess) return e;
   if (P.ntiles <= 0) return cudaSuccess;
   const long long pairs = std::min<long long>(P.ntiles, max_pairs());
   crt_gemm_kernel<<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
@@ -2076,11 +2082,19 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
     }
   }
   const int slices = choose_slices(ctx->opt.target_rel_err, ctx->opt.slices);
+  // the form of the whole batch (every k-point has the same depth)
+  const SplitPlan pl = split_plan(ctx, ctx->depth);
+  const bool crt = pl.scheme == kSchemeModuli;
+  const int units = crt ? pl.nmod : slices;  // planes per operand part: moduli or slices
+  const CrtConsts cc = crt ? make_crt(pl.nmod) : CrtConsts{};
+  const int bn = crt ? BNC : BN;
+  const int tband = crt ? std::max(1, ctx->tile_band * BN / BNC) : ctx->tile_band;
+  ctx->last_plan = pl;
   if (ctx->split_slices != slices) {
     hsgen_status st = split_prepare_types(ctx, slices);
     if (st != HSGEN_OK) return st;
   }
-  HSG_CUDA(ctx, cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  HSG_CUDA(ctx, gemm_attrs());
   // S in the Legendre form: every k-point must lie on its lattice k + G
   // (otherwise the caller's k-point loop takes over, per k-point)
   const bool leg = ctx->opt.s_form == HSGEN_S_LEGENDRE;
@@ -2091,17 +2105,26 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   const long long ldk = round_up(depth, BK);
   const int nt = (int)ctx->types.size();
   const int uplo = ctx->opt.uplo;
-  const int nkb_all = (int)(ldk / BK), seg_kb = std::max(1, ctx->kseg_blocks);
+  const int nkb_all = (int)(ldk / BK);
+  const int seg_kb = crt ? std::max(1, std::min(ctx->kseg_blocks, 256)) : std::max(1, ctx->kseg_blocks);
   const int nseg = (nkb_all + seg_kb - 1) / seg_kb;
   auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
   // ---- plan: groups of k-points whose slices fit the budget
   size_t budget = (size_t)96 << 30;
   if (const char *e = std::getenv("HSGEN_BATCH_BYTES")) budget = (size_t)std::max(1.0, std::atof(e));
-  std::vector<size_t> kslice(n_k);
+  // per k-point: 8 planes per slice or modulus (W 3, X 3, U W 2), and in the
+  // moduli form its residue store (H and S tiles)
+  std::vector<size_t> kslice(n_k), kstore(n_k, 0);
+  std::vector<long long> kslots(n_k, 0);
   int max_ng = 1;
   long long sum_ng = 0;
   for (int k = 0; k < n_k; ++k) {
-    kslice[k] = al((size_t)8 * slices * n_g[k] * ldk * sizeof(__nv_bfloat16));
+    kslice[k] = al((size_t)8 * units * n_g[k] * ldk * sizeof(__nv_bfloat16));
+    if (crt && n_g[k] > 0) {
+      kslots[k] = crt_tile_count(n_g[k], uplo);
+      kstore[k] = al((size_t)2 * kslots[k] * pl.nmod * 65536);
+      kslice[k] += kstore[k];
+    }
     max_ng = std::max(max_ng, n_g[k]);
     sum_ng += n_g[k];
   }
@@ -2117,7 +2140,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   std::vector<std::vector<int2>> tl(n_k);
   size_t n_tl = 0;
   for (int k = 0; k < n_k; ++k) {
-    if (n_g[k] > 0) tl[k] = tri_tiles(n_g[k], uplo, ctx->tile_band);
+    if (n_g[k] > 0) tl[k] = tri_tiles(n_g[k], uplo, tband, bn);
     n_tl += tl[k].size();
   }
   // ---- workspace layout
@@ -2206,15 +2229,20 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
       for (int k = groups[gi].first; k < groups[gi].second; ++k) {
         if (n_g[k] <= 0) continue;
         const long long plane = (long long)n_g[k] * ldk;
-        __nv_bfloat16 *Wsl = slice_base(k, (int)gi), *Xsl = Wsl + 3 * slices * plane, *Ysl = Xsl + 3 * slices * plane;
+        __nv_bfloat16 *Wsl = slice_base(k, (int)gi), *Xsl = Wsl + 3 * units * plane, *Ysl = Xsl + 3 * units * plane;
+        unsigned char *store = (unsigned char *)slice_base(k, (int)gi) + (kslice[k] - kstore[k]);
         int *eW = d_exp + 3 * kv_off[k], *eX = eW + n_g[k], *eY = eX + n_g[k];
         GemmProblem pr2[2];
         CUtensorMap ma[2], mb[2];
         const long long nt_k = (long long)tl[k].size();
-        if (!hs_problems(pr2, ma, mb, n_g[k], ldk, kb0, seg, false, uplo, Wsl, Xsl, Ysl, eW, eX, eY,
-                         (double2 *)H[k], leg ? nullptr : (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k, tiles,
-                         slices))
-          return set_err(ctx, HSGEN_ECUDA, "batched: cuTensorMapEncodeTiled failed");
+        const bool ok =
+            crt ? crt_problems(pr2, ma, mb, n_g[k], ldk, kb0, seg, nkb_all, false, uplo, Wsl, Xsl, Ysl, eW, eX, eY,
+                               (double2 *)H[k], leg ? nullptr : (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k,
+                               tiles, 0, kslots[k], store, pl.nmod, pl.bits)
+                : hs_problems(pr2, ma, mb, n_g[k], ldk, kb0, seg, false, uplo, Wsl, Xsl, Ysl, eW, eX, eY,
+                              (double2 *)H[k], leg ? nullptr : (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k, tiles,
+                              slices);
+        if (!ok) return set_err(ctx, HSGEN_ECUDA, "batched: cuTensorMapEncodeTiled failed");
         const int np_k = leg ? 1 : 2;  // H (and S) of this k-point
         for (int j = 0; j < np_k; ++j) {
           hprob[pi] = pr2[j];
@@ -2238,7 +2266,8 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
       hsgen_status st = legendre_upload(ctx, n_g[k], plans[k], ws + o_leg[k], s);
       if (st != HSGEN_OK) return st;
     }
-  std::vector<long long> key = {(long long)(uintptr_t)ws, (long long)slices, (long long)uplo, (long long)n_k,
+  std::vector<long long> key = {(long long)(uintptr_t)ws, (long long)slices, (long long)pl.scheme, (long long)pl.nmod,
+                                (long long)uplo, (long long)n_k,
                                 (long long)ctx->kseg_blocks, (long long)ctx->tile_band, (long long)leg};
   for (int k = 0; k < n_k; ++k) {
     key.push_back(n_g[k]);
@@ -2268,8 +2297,8 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           if (ng <= 0) continue;
           const double *kd = d_kv + 3 * kv_off[k];
           const long long plane = (long long)ng * ldk;
-          __nv_bfloat16 *Wsl = slice_base(k, (int)gi), *Xsl = Wsl + 3 * slices * plane,
-                        *Ysl = Xsl + 3 * slices * plane;
+          __nv_bfloat16 *Wsl = slice_base(k, (int)gi), *Xsl = Wsl + 3 * units * plane,
+                        *Ysl = Xsl + 3 * units * plane;
           int *eW = d_exp + 3 * kv_off[k], *eX = eW + ng, *eY = eX + ng;
           double2 *Fk = leg ? F + (size_t)nt * kv_off[k] * kRadStride : F;
           HSG_LAUNCH(ctx, launch_radial(ng, kd, nt, ctx->d_radial, Fk, s));
@@ -2280,12 +2309,22 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
                                                 ctx->d_atoms_by_type + ctx->atoms_by_type_start[t], n, ctx->d_pos,
                                                 ctx->d_rot, ctx->d_off, 0, ctx->types[t].dpad, W, depth, s));
           }
-          HSG_LAUNCH(ctx, launch_slice(W, depth, depth, nullptr, slices, 3, Wsl, ldk, plane, eW, ng, s));
-          hsgen_status st2 = tapply_split(ctx, ng, 0, na, Wsl, ldk, eW, X, depth, slices, s);
+          // W's slices for X = T W; in the moduli form they sit in X's residue planes, written after
+          __nv_bfloat16 *Wfx = crt ? Xsl : Wsl;
+          HSG_LAUNCH(ctx, launch_slice(W, depth, depth, nullptr, slices, 3, Wfx, ldk, plane, eW, ng, s));
+          hsgen_status st2 = tapply_split(ctx, ng, 0, na, Wfx, ldk, eW, X, depth, slices, s);
           if (st2 != HSGEN_OK) return st2;
-          HSG_LAUNCH(ctx, launch_slice(X, depth, depth, nullptr, slices, 3, Xsl, ldk, plane, eX, ng, s));
-          if (!leg)
-            HSG_LAUNCH(ctx, launch_slice(W, depth, depth, ctx->d_urow, slices, 2, Ysl, ldk, plane, eY, ng, s));
+          if (crt) {
+            HSG_LAUNCH(ctx, launch_residue(X, depth, depth, nullptr, pl.bits, cc, 3, Xsl, ldk, plane, eX, ng, s));
+            HSG_LAUNCH(ctx, launch_residue(W, depth, depth, nullptr, pl.bits, cc, 3, Wsl, ldk, plane, eW, ng, s));
+            if (!leg)
+              HSG_LAUNCH(ctx, launch_residue(W, depth, depth, ctx->d_urow, pl.bits, cc, 2, Ysl, ldk, plane, eY, ng,
+                                             s));
+          } else {
+            HSG_LAUNCH(ctx, launch_slice(X, depth, depth, nullptr, slices, 3, Xsl, ldk, plane, eX, ng, s));
+            if (!leg)
+              HSG_LAUNCH(ctx, launch_slice(W, depth, depth, ctx->d_urow, slices, 2, Ysl, ldk, plane, eY, ng, s));
+          }
         }
         for (int sg = 0; sg < nseg; ++sg) {
           const size_t li = gi * nseg + sg;
@@ -2299,7 +2338,12 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           P.s = slices;
           P.status = ctx->d_status;
           P.timeout_ns = (unsigned long long)ctx->opt.wait_timeout_ns;
-          HSG_LAUNCH(ctx, launch_gemm(P, s));
+          if (crt) {
+            P.crt = cc;
+            HSG_LAUNCH(ctx, launch_crt(P, s));
+          } else {
+            HSG_LAUNCH(ctx, launch_gemm(P, s));
+          }
         }
         // Legendre form: S, and H's spherical tail added after the contraction wrote H
         for (int k = groups[gi].first; k < groups[gi].second && leg; ++k) {
@@ -2334,6 +2378,11 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   HSG_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, s));
   ctx->stats.slices = slices;
   ctx->stats.precision = HSGEN_SPLIT;
+  ctx->stats.scheme = crt ? HSGEN_SCHEME_MODULI : HSGEN_SCHEME_SLICES;
+  ctx->stats.moduli = pl.nmod;
+  ctx->stats.bits = pl.bits;
+  ctx->stats.products = crt ? pl.nmod : slices * (slices + 1) / 2;
+  ctx->stats.atom_chunks = 1;
   ctx->phase_used[0] = 0;
   ctx->phase_used[1] = 0;
   ctx->phase_used[2] = 0;

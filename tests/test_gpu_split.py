@@ -352,7 +352,7 @@ def test_autotune_picks_the_form_by_measured_error(hs, target):
         assert st["scheme"] == hs.SCHEME_SLICES and st["slices"] == 7
     # the measured figure is the real error (to the reference's ~1e-15)
     (hf, _), (sf, _), _ = errors(w.system, w.kvecs[0], H.cpu().numpy(), S.cpu().numpy())
-    assert max(hf, sf) <= max(2.0 * st["tuned_rel_err"], 1e-14)
+    assert max(hf, sf) <= 2.0 * st["tuned_rel_err"] + 1e-13
 
 
 def test_split_timeout_is_reported_and_context_recovers(hs):
