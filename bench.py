@@ -1,19 +1,32 @@
 """Benchmark of the muffin-tin H+S generator (one JSON line on rank 0).
 
 Metric: seconds per k-point to build H and S (and the effective TFLOP/s of
-that build), split-precision form vs the FP64 form, on one GB300.
+that build), split-precision form vs the FP64 form, on one GB300, at the
+metric's accuracy (relative Frobenius error <= 1e-11).
 
 A step is one pass of the whole path (radial factors, A/B coefficients,
 X = T W, the H/S contraction) for one k-point of the chosen workload; inputs
 are resident in HBM before the timed region. Default workload: 256 atoms of
-4 species, l_max 10, N_G 20000 (H and S 6.4 GB each). The timed region uses
-CUDA events on the launching stream after W warm-up steps; the working set
-(W, X and the slices, tens of GB) is far larger than the 129 MB L2, so no
-flush is needed between steps.
+4 species, l_max 10, N_G 20000 (H and S 6.4 GB each). Before the warm-up,
+hsgen_autotune (untimed) picks the split form (slices or moduli, by the
+error it measures against a 7-slice build and by time) and the schedule for
+--target (default 1e-11). The timed region uses CUDA events on the
+launching stream after W warm-up steps; the working set (W, X and the
+operand planes, tens of GB) is far larger than the 129 MB L2, so no flush
+is needed between steps.
 
-Multi-GPU (torchrun): k-points are independent, so every rank builds its own
-k-point (replicas, weak scaling, no data-path collective); the barrier and
-the max over ranks are only for timing.
+After the timed region (not timed): `error`, whole columns of the timed H
+and S against the oracle (relative Frobenius and largest per-entry error);
+`fp64_form`, one timed build of the plain FP64 form on the same workload
+with its own error (--no-fp64-compare skips it: about 3 minutes); `e2e`,
+the same build through the C ABI from and to pinned host memory;
+`cpu_baseline`, the oracle on a bounded sample.
+
+Multi-GPU (torchrun): a multi-k-point workload deals its k-points
+round-robin; a single k-point is split 2-D block-cyclically over the ranks
+(hsgen_build_HS_blocks, strong scaling; --replicas: every rank builds the
+whole k-point, weak scaling). No data-path collective; the barrier and the
+max over ranks are only for timing.
 
 --impl reference times the oracle (plain FP64 CPU code) on the host cores on
 a bounded sample of the same workload, extrapolated to one k-point.
@@ -260,10 +273,15 @@ def run_batched(args, w, world, rank, local, dist):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     s_form = hsgen.S_LEGENDRE if args.s_form == "legendre" else hsgen.S_CONTRACTION
-    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form)
+    g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form,
+                        target_rel_err=args.target, scheme=SCHEMES[args.scheme], moduli=args.moduli)
     kv_host = [np.ascontiguousarray(w.kvecs[k]) for k in mine]
     Hs = [torch.zeros((n, n), dtype=torch.complex128, device=dev) for n in n_gs]
     Ss = [torch.zeros_like(h) for h in Hs]
+    if precision == hsgen.SPLIT and not args.no_autotune and n_gs:
+        # untimed: form and schedule tuned on the largest k-point of the batch
+        kbig = int(np.argmax(n_gs))
+        g.autotune(torch.from_numpy(kv_host[kbig]).to(dev), Hs[kbig], Ss[kbig])
 
     def step():
         hsgen.hsgen_build_HS_batched(g.ctx, n_gs, [k.ctypes.data for k in kv_host], [h.data_ptr() for h in Hs],
@@ -301,6 +319,26 @@ def run_batched(args, w, world, rank, local, dist):
     clk_s = clk.summary()
     if clk_s:
         line["clocks"] = clk_s
+    st = g.stats()
+    line["config"]["scheme"] = {1: "slices (Ozaki I)", 2: "moduli (Ozaki II)"}.get(st["scheme"])
+    line["config"]["bf16_products_per_fp64_product"] = st["products"]
+    if not args.no_sequential and precision == hsgen.SPLIT:
+        # the same k-points as separate hsgen_build_HS calls (one k-point each, same context)
+        kv_dev = [torch.from_numpy(k).to(dev) for k in kv_host]
+        for k in range(len(n_gs)):
+            g.build(kv_dev[k], Hs[k], Ss[k])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for k in range(len(n_gs)):
+                g.build(kv_dev[k], Hs[k], Ss[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1) / args.steps
+        line["sequential"] = {"s_per_kpoint": seq_ms * 1e-3 / max(1, len(n_gs)), "ms_per_step": seq_ms,
+                              "batched_speedup": seq_ms / ms,
+                              "how": "one hsgen_build_HS call per k-point, same context and schedule"}
     g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -594,6 +632,11 @@ def main():
                     help="split form: relative error the slice or moduli count is chosen for (the metric's 1e-11)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="multi-k-point workload: skip timing the k-points as separate hsgen_build_HS calls")
+    ap.add_argument("--replicas", action="store_true",
+                    help="several GPUs, one k-point: every rank builds the whole k-point (weak scaling) instead of "
+                         "its 2-D block-cyclic blocks")
     ap.add_argument("--ref-columns", type=int, default=384)
     ap.add_argument("--n-g", type=int, default=0, help="override N_G (smaller cases for profiling)")
     ap.add_argument("--no-fp64-compare", action="store_true",
@@ -673,10 +716,27 @@ def main():
     H = torch.zeros((n, n), dtype=torch.complex128, device=dev)
     S = torch.zeros_like(H)
     if precision == hsgen.SPLIT and not args.no_autotune:
-        g.autotune(kv, H, S)  # untimed: picks the depth segment and tile band for this shape
+        g.autotune(kv, H, S)  # untimed: picks the split form, the depth segment and the tile band
     tuned = g.stats()
+    # several ranks and one k-point: the k-point's H and S split 2-D
+    # block-cyclically over the most square process grid (strong scaling);
+    # --replicas: every rank builds the whole k-point (weak scaling)
+    from paper_1602_06589_gb300 import partition
+
+    blocks = world > 1 and not args.replicas
+    prow, pcol = partition.grid_shape(world)
+    myrow, mycol = divmod(rank, pcol)
+    BLOCK = 256
+
+    def build():
+        if blocks:
+            hsgen.hsgen_build_HS_blocks(g.ctx, n, kv.data_ptr(), H.data_ptr(), S.data_ptr(), n, BLOCK, prow, pcol,
+                                        myrow, mycol, stream.cuda_stream)
+        else:
+            g.build(kv, H, S)
+
     for _ in range(args.warmup):
-        g.build(kv, H, S)
+        build()
     torch.cuda.synchronize()
     contract_ms, launches = [], 0
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -686,7 +746,7 @@ def main():
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            g.build(kv, H, S)
+            build()
             st = g.stats()  # reads the library's own events (recorded on this stream)
             contract_ms.append(st["ms_contract"])
             launches += st["kernel_launches"]
@@ -700,7 +760,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     st = g.stats()
-    s_per_k = ms * 1e-3 / world  # every rank builds one k-point per step
+    s_per_k = ms * 1e-3 if blocks else ms * 1e-3 / world  # one k-point over all ranks, or one per rank
     eff_tflops = fal["total"] / (ms * 1e-3) / 1e12
     peaks = _peaks()
 
@@ -722,7 +782,8 @@ def main():
 
     line = {
         "metric": METRIC, "value": s_per_k, "unit": "s/k-point", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "strong" if blocks else "weak",
         "vs_baseline": None, "dtype": "bf16-split/f64" if precision == hsgen.SPLIT else "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(args.config, w), "form": args.form,
@@ -738,8 +799,13 @@ def main():
                    "target_rel_err": args.target if precision == hsgen.SPLIT else None,
                    "atom_chunks": st["atom_chunks"],
                    "schedule": ({"kseg_blocks": tuned["kseg_blocks"], "tile_band": tuned["tile_band"],
-                                 "autotuned": not args.no_autotune} if precision == hsgen.SPLIT else None),
-                   "l2": "working set >> L2 (no flush needed)", "parallelism": f"k-point replicas x{world}"},
+                                 "stage_geometry": tuned["stage_geometry"],
+                                 "autotuned": not args.no_autotune,
+                                 "autotune_measured_rel_err": tuned["tuned_rel_err"]}
+                                if precision == hsgen.SPLIT else None),
+                   "l2": "working set >> L2 (no flush needed)",
+                   "parallelism": (f"one k-point, H/S blocks of {BLOCK} 2-D block-cyclic over a {prow} x {pcol} grid"
+                                   if blocks else f"k-point replicas x{world}")},
         "eff_tflops": eff_tflops, "flops_per_kpoint": fal["total"],
         "phases_ms": {k: st[k] for k in ("ms_coefficients", "ms_tapply", "ms_slice", "ms_contract", "ms_s", "ms_total")},
         "roofline": roof, "gpu_launches": launches,
@@ -747,7 +813,34 @@ def main():
     if clk_s:
         line["clocks"] = clk_s
 
-    if not args.no_e2e:
+    if not args.no_e2e and blocks:
+        # end to end, one k-point over the grid: K_t from pinned host memory,
+        # the rank's blocks built, its block columns copied to pinned host memory
+        kh = torch.from_numpy(kv_host.copy()).pin_memory()
+        mine = [J for J in range((n + BLOCK - 1) // BLOCK) if J % pcol == mycol]
+        Hh = torch.empty((len(mine) * BLOCK, n), dtype=torch.complex128).pin_memory()
+        Sh = torch.empty_like(Hh).pin_memory()
+        e_steps = max(1, min(args.steps, 3))
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            kv.copy_(kh, non_blocking=True)
+            build()
+            r0 = 0
+            for J in mine:
+                c0, c1 = J * BLOCK, min(n, (J + 1) * BLOCK)
+                Hh[r0:r0 + c1 - c0].copy_(H[c0:c1], non_blocking=True)  # row c of the buffer = column c
+                Sh[r0:r0 + c1 - c0].copy_(S[c0:c1], non_blocking=True)
+                r0 += c1 - c0
+            torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / e_steps
+        t = torch.tensor([te], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": float(t.item()), "unit": "s/k-point", "h2d_bytes_per_step": int(kh.numel() * 8),
+                       "d2h_bytes_per_step": int(2 * sum(min(n, (J + 1) * BLOCK) - J * BLOCK for J in mine) * n * 16),
+                       "note": "per rank: its block columns (all rows) of H and S"}
+        del Hh, Sh
+    elif not args.no_e2e:
         # end to end through the C ABI with host buffers (copies inside the timed region)
         kh = torch.from_numpy(kv_host.copy()).pin_memory()
         Hh = torch.empty((n, n), dtype=torch.complex128).pin_memory()

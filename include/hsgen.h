@@ -39,8 +39,11 @@
  * them on one stream, or synchronise between streams.
  * Buffers on another GPU than the context's are rejected (HSGEN_EINVAL).
  * Environment (tuning only; results move at the rounding level at most):
- * HSGEN_KSEG_BLOCKS, the split form's depth segment in 64-deep blocks (read
- * by hsgen_create; hsgen_autotune picks one per shape); HSGEN_BATCH_BYTES,
+ * HSGEN_KSEG_BLOCKS, the split form's depth segment in 64-deep blocks, and
+ * HSGEN_CRT_GEOMETRY (0 or 1), the moduli kernel's stage geometry (both read
+ * by hsgen_create; hsgen_autotune picks them per shape); HSGEN_WS_BYTES, the
+ * split form's workspace budget that sets the passes over the atoms when
+ * opt.atom_chunk is 0 (default 176e9); HSGEN_BATCH_BYTES,
  * the slice-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
  * block rows of the split-form hsgen_reduce_generalized (default 256).
  * Fault injection (tests): HSGEN_FAIL_ALLOC=1 makes every growth of a
@@ -157,6 +160,8 @@ typedef struct {
   double tuned_rel_err;    /* hsgen_autotune: relative Frobenius error of the   */
                            /* chosen form against a 7-slice build (0: not       */
                            /* measured)                                         */
+  int stage_geometry;      /* moduli scheme: pipeline stages of its kernel, 0:  */
+                           /* three of two 64-deep blocks, 1: two of three      */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -266,7 +271,8 @@ hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
  * the a-priori choice; of the two, the faster build on this GPU is kept
  * (hsgen_stats tuned_rel_err reports its error). (2) The schedule: times builds for
  * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 (tile band 16),
- * then tile bands {8, 32} with the best segment. The choices stay in the
+ * then tile bands {8, 32} with the best segment, then, for the moduli scheme,
+ * its kernel's other stage geometry (hsgen_stats stage_geometry). The choices stay in the
  * context for later builds (batched ones use the schedule) and H and S are
  * left built with them. Same arguments as hsgen_build_HS; synchronous; about
  * ten to fifteen builds long. The FP64 form has nothing to tune: it builds

@@ -210,6 +210,7 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   ctx->device = cuda_device;
   ctx->opt = o;
   if (const char *ks = std::getenv("HSGEN_KSEG_BLOCKS")) ctx->kseg_blocks = std::max(1, std::atoi(ks));
+  if (const char *cg = std::getenv("HSGEN_CRT_GEOMETRY")) ctx->crt_geom = std::atoi(cg) == 1 ? 1 : 0;
   if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess ||
       split_upload_tables() != cudaSuccess) {
     delete ctx;
@@ -1007,6 +1008,21 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
       best_b = band;
     }
   }
+  // moduli scheme: the stage geometry of its kernel (3 stages of 2 k-blocks
+  // or 2 stages of 3)
+  if (ctx->last_plan.scheme == kSchemeModuli) {
+    const int g0 = ctx->crt_geom;
+    int best_g = g0;
+    ctx->crt_geom = 1 - g0;
+    double ms = 0.0;
+    hsgen_status st = trial(best_k, best_b, ms);
+    if (st != HSGEN_OK) return st;
+    if (ms < best) {
+      best = ms;
+      best_g = 1 - g0;
+    }
+    ctx->crt_geom = best_g;
+  }
   ctx->kseg_blocks = best_k;
   ctx->tile_band = best_b;
   const double tuned = ctx->stats.tuned_rel_err;
@@ -1046,6 +1062,7 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   st.workspace_bytes = (long long)(ctx->ws_main.bytes + ctx->ws_out.bytes + ctx->ws_leg.bytes);
   st.kseg_blocks = ctx->kseg_blocks;
   st.tile_band = ctx->tile_band;
+  st.stage_geometry = ctx->crt_geom;
   *out = st;
   // the stats are filled in either way; a wait that expired is reported here
   return split_poll_status(ctx, true);

@@ -735,7 +735,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 // The launch that ends the depth reconstructs C' from the residues (128-bit
 // integers), scales it to FP64 and writes (or adds) the tile of H or S.
 constexpr int BNC = 128;  // complex output columns of a moduli-form tile
-constexpr int CKB = 8;    // 64-deep k-blocks per accumulation chunk (x 2 halves = 1024 products)
+// stage geometries of the moduli kernel: (k-blocks per stage, stages, k-blocks
+// per accumulation chunk); a chunk holds at most 1024 products (exact in FP32)
+struct CrtGeom {
+  int kps, nst, ckb;
+};
+constexpr CrtGeom kCrtGeoms[2] = {{2, 3, 8}, {3, 2, 6}};
 
 __device__ __forceinline__ Tile decode_tile_crt(const GemmParams &P, long long t, long long &slot) {
   int pi = 0, hi = P.nprob;
@@ -780,8 +785,14 @@ __device__ __forceinline__ int mod_small(int a, int m, float inv_m) {
   return r;
 }
 
+template <int KPS_, int NST_, int CKB_>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     crt_gemm_kernel(const __grid_constant__ GemmParams P) {
+  // stage geometry: KPS_ k-blocks per stage, NST_ stages, CKB_ k-blocks per chunk
+  constexpr int KPS = KPS_, NST = NST_, CKB = CKB_;
+  constexpr int STAGE_A = KPS * A_BYTES, STAGE_BYTES = KPS * (A_BYTES + B_BYTES);
+  static_assert(CKB % KPS == 0 && CKB * BK * 2 <= 1024 && NST * STAGE_BYTES + 1024 + 256 <= SMEM_BYTES,
+                "stage geometry");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES);
@@ -976,7 +987,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         // of the earlier depth segments
         const int m = P.crt.m[i];
         const float inv = P.crt.inv_m[i];
-        const int off = m << 22;  // makes every sum non-negative (|sum| <= 32 chunks x 2^24)
+        const int off = m << 22;  // makes every sum non-negative (|sum| <= 256 x 128 products x 2^14)
 #pragma unroll
         for (int u = 0; u < 128; ++u) acc[u] = mod_small(acc[u] + off, m, inv);
         uint4 *rp = res_ptr(i);
@@ -1303,7 +1314,9 @@ cudaError_t gemm_attrs() {
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(crt_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      e = cudaFuncSetAttribute(crt_gemm_kernel<2, 3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(crt_gemm_kernel<3, 2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -1319,12 +1332,15 @@ cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_crt(GemmParams &P, cudaStream_t s) {
+cudaError_t launch_crt(GemmParams &P, int geom, cudaStream_t s) {
   cudaError_t e = gemm_attrs();
   if (e != cudaSuccess) return e;
   if (P.ntiles <= 0) return cudaSuccess;
   const long long pairs = std::min<long long>(P.ntiles, max_pairs());
-  crt_gemm_kernel<<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
+  if (geom == 1)
+    crt_gemm_kernel<3, 2, 6><<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
+  else
+    crt_gemm_kernel<2, 3, 8><<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
   return cudaGetLastError();
 }
 
@@ -1953,7 +1969,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
                           cw.Yr, cw.expW, cw.expX, cw.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, t0,
                           slots, cw.store, pl.nmod, pl.bits))
           return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S, moduli)");
-        HSG_LAUNCH(ctx, launch_crt(P, s));
+        HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s));
         return HSGEN_OK;
       }
       if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
@@ -2340,7 +2356,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           P.timeout_ns = (unsigned long long)ctx->opt.wait_timeout_ns;
           if (crt) {
             P.crt = cc;
-            HSG_LAUNCH(ctx, launch_crt(P, s));
+            HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s));
           } else {
             HSG_LAUNCH(ctx, launch_gemm(P, s));
           }
