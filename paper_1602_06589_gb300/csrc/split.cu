@@ -772,6 +772,16 @@ __device__ __forceinline__ void st_v4(uint4 *p, const uint32_t (&w)[4]) {
                : "memory");
 }
 
+// a mod m for 0 <= a < 2^26, 2 <= m <= 256: the truncated float quotient
+// is within one of the true one (the roundings of a, of 1/m and of the
+// product move a / m by less than 0.05), so one correction each way suffices
+__device__ __forceinline__ int mod_small26(int a, int m, float inv_m) {
+  const int q = __float2int_rz(__int2float_rz(a) * inv_m);
+  int r = a - q * m;
+  r = (r < 0) ? r + m : r;
+  return (r >= m) ? r - m : r;
+}
+
 // a mod m for 0 <= a < 2^31, 2 <= m <= 256: the float quotient is within 3
 // of the true one (rounding of a, of 1/m and of the product), then corrected
 __device__ __forceinline__ int mod_small(int a, int m, float inv_m) {
@@ -1222,7 +1232,7 @@ __global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict_
       float r[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        int x = mod_small(p2[q] * c32 + p1[q] * c16 + p0[q], m, crt.inv_m[i]);  // |N| mod m (< 2^25 in)
+        int x = mod_small26(p2[q] * c32 + p1[q] * c16 + p0[q], m, crt.inv_m[i]);  // |N| mod m (< 2^25 in)
         if (ng[q] && x) x = m - x;                                              // N mod m
         r[q] = (float)((2 * x > m) ? x - m : x);                                // balanced, |r| <= 128
       }

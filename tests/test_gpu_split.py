@@ -164,6 +164,21 @@ def test_moduli_error_follows_the_bits(hs):
     assert errs[3][1] < errs[2][1], errs  # 47 bits: the floor of X = T W
 
 
+def test_moduli_stage_geometries_agree_bitwise(hs, monkeypatch):
+    """The moduli kernel's two stage geometries (3 stages of 2 k-blocks with
+    chunks of 8, 2 stages of 3 with chunks of 6) sum the same exact integers,
+    so H and S agree bit for bit."""
+    w = make_config(1)
+    out = []
+    for geom in ("0", "1"):
+        monkeypatch.setenv("HSGEN_CRT_GEOMETRY", geom)
+        H, S, st = run_gpu(hs, w.system, w.kvecs[0], scheme=hs.SCHEME_MODULI)
+        assert st["stage_geometry"] == int(geom)
+        out.append((H, S))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    check(w.system, w.kvecs[0], *out[1])
+
+
 def test_moduli_across_many_depth_segments(hs, monkeypatch):
     """One depth segment of 64 rows per launch (41 launches at 16 atoms /
     N_G 3000): the residues of every segment add up modulo each m_i in the
