@@ -10,7 +10,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -990,10 +989,7 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   };
   int best_k = ctx->kseg_blocks, best_b = ctx->tile_band;
   double best = 1e300;
-  const std::initializer_list<int> segs = ctx->last_plan.scheme == kSchemeModuli
-                                               ? std::initializer_list<int>{128, 64, 256, 512}
-                                               : std::initializer_list<int>{128, 64, 96, 192, 256};
-  for (int kseg : segs) {
+  for (int kseg : {128, 64, 96, 192, 256}) {
     double ms = 0.0;
     hsgen_status st = trial(kseg, 16, ms);
     if (st != HSGEN_OK) return st;

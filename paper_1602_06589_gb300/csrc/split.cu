@@ -727,16 +727,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 //
 // Tiles are 256 output rows x 128 complex columns (CTA pair, M = 256): every
 // MMA is N = 256, the B operand [Qr | Qi] (r half) or [Qi | -Qr] (i half)
-// split by rows between the two CTAs. The depth runs in chunks of at most
-// 1024 products (exact in FP32), every modulus per chunk before the next
-// chunk (so the operands a wave of tiles shares stay a few k-blocks apart
-// and hit in L2), into one of two TMEM accumulators; the epilogue reduces
-// each chunk mod m_i in FP32 (exact: the sums are integers below 2^24) and
-// adds it, mod m_i, to the tile's residue bytes, a per-tile store in global
-// memory that stays in L2 while the tile runs and carries the residues
-// across depth segments (separate launches). The launch that ends the depth
-// reconstructs C' from the residues (128-bit integers), scales it to FP64
-// and writes (or adds) the tile of H or S.
+// split by rows between the two CTAs. Per modulus the depth runs in chunks
+// of 1024 products (exact in FP32) into one of two TMEM accumulators; the
+// epilogue adds each chunk into int32 sums in registers, reduces them mod m_i
+// at the end of the modulus and keeps the residue bytes in a per-tile store
+// in global memory, added mod m_i across depth segments (separate launches).
+// The launch that ends the depth reconstructs C' from the residues (128-bit
+// integers), scales it to FP64 and writes (or adds) the tile of H or S.
 constexpr int BNC = 128;  // complex output columns of a moduli-form tile
 // stage geometries of the moduli kernel: (k-blocks per stage, stages, k-blocks
 // per accumulation chunk); a chunk holds at most 1024 products (exact in FP32)
@@ -783,6 +780,19 @@ __device__ __forceinline__ int mod_small26(int a, int m, float inv_m) {
   int r = a - q * m;
   r = (r < 0) ? r + m : r;
   return (r >= m) ? r - m : r;
+}
+
+// a mod m for 0 <= a < 2^31, 2 <= m <= 256: the float quotient is within 3
+// of the true one (rounding of a, of 1/m and of the product), then corrected
+__device__ __forceinline__ int mod_small(int a, int m, float inv_m) {
+  const int q = __float2int_rz(__int2float_rz(a) * inv_m);
+  int r = a - q * m;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r = (r < 0) ? r + m : r;
+    r = (r >= m) ? r - m : r;
+  }
+  return r;
 }
 
 template <int KPS_, int NST_, int CKB_>
@@ -841,10 +851,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const Tile ti = decode_tile_crt(P, t, slot);
       const GemmProblem &pr = problem(P, ti.prob);
       const CUtensorMap *mA = map_a(P, ti.prob), *mB = map_b(P, ti.prob);
-      for (int kc0 = 0; kc0 < ti.nkb && ok; kc0 += CKB)
-        for (int i = 0; i < NM && ok; ++i)
-        for (int kb = kc0; kb < min(ti.nkb, kc0 + CKB) && ok; kb += KPS) {
-          const int nk = min(KPS, min(ti.nkb, kc0 + CKB) - kb);
+      for (int i = 0; i < NM && ok; ++i)
+        for (int kb = 0; kb < ti.nkb && ok; kb += KPS) {
+          const int nk = min(KPS, ti.nkb - kb);
           const uint32_t bytes = nk * 2 * (A_BYTES + B_BYTES);
           for (int h = 0; h < 2; ++h, ++it) {
             const int st = it % NST;
@@ -886,8 +895,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       for (long long t = pair; t < P.ntiles && ok; t += npairs) {
         long long slot;
         const Tile ti = decode_tile_crt(P, t, slot);
-        for (int kc0 = 0; kc0 < ti.nkb && ok; kc0 += CKB)
-          for (int i = 0; i < NM && ok; ++i, ++cc) {
+        for (int i = 0; i < NM && ok; ++i)
+          for (int kc0 = 0; kc0 < ti.nkb && ok; kc0 += CKB, ++cc) {
             const int kc1 = min(ti.nkb, kc0 + CKB);
             const int buf = cc % NACC;
             const uint32_t use = cc / NACC;
@@ -939,7 +948,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // ------------------------------ epilogue ----------------------------------
     // Warp w: TMEM lane quadrant w % 4 (rows), accumulator half hf = w / 4
     // (hf 0: real parts, hf 1: imaginary parts of the tile's 128 columns);
-    // each thread owns its row's 128 residue bytes per modulus in the store.
+    // each thread holds the int32 sums of its row's 128 values.
     const int qd = warp & 3;
     const int hf = warp >> 2;
     const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
@@ -954,8 +963,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       auto res_ptr = [&](int i) {
         return (uint4 *)(pr.res + ((((size_t)slot * NM + i) * 2 + rank) * 256 + threadIdx.x) * 128);
       };
-      for (int kc = 0; kc < nkc && ok; ++kc)
-        for (int i = 0; i < NM && ok; ++i, ++cc) {
+      for (int i = 0; i < NM && ok; ++i) {
+        int acc[128];
+#pragma unroll
+        for (int u = 0; u < 128; ++u) acc[u] = 0;
+        for (int kc = 0; kc < nkc && ok; ++kc, ++cc) {
           const int buf = cc % NACC;
           const uint32_t use = cc / NACC;
           int got = 0;
@@ -967,45 +979,47 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          // chunk sums (exact integers |v| <= 2^24 in FP32) mod m_i, added mod
-          // m_i to the tile's residue bytes (hot in L2 while the tile runs)
-          const float mf = (float)P.crt.m[i], inv = P.crt.inv_m[i];
-          const bool fresh = pr.seg_first && kc == 0;
           const uint32_t tacc = tbase + lane_off + buf * 256 + hf * 128;
-          uint4 *rp = res_ptr(i);
           uint32_t v[16];
-#pragma unroll 1
-          for (int g = 0; g < 8; ++g) {
-            tc_ld16(tacc + g * 16, v);
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (!fresh) ld_v4(rp + g, w);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            tc_ld16(tacc + q * 16, v);
             tc_wait_ld();
-            if (g == 7) {  // every TMEM column of this buffer has been read
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive_cluster(lead_acce0 + 8 * buf);
-            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              uint32_t outw = 0;
-#pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                const float x = __uint_as_float(v[q * 4 + b]);
-                // nearest integer to x / m (within one of the floor), then the exact remainder
-                const float qf = __fmaf_rn(x, inv, 12582912.0f) - 12582912.0f;
-                float r = __fmaf_rn(-qf, mf, x);
-                r = (r < 0.0f) ? r + mf : r;
-                r = (r >= mf) ? r - mf : r;
-                // + the residue so far (a byte, made a float exactly)
-                r += __int_as_float(0x4B000000 | ((w[q] >> (8 * b)) & 0xFFu)) - 8388608.0f;
-                r = (r >= mf) ? r - mf : r;
-                outw |= (uint32_t)(__float_as_int(r + 8388608.0f) & 0xFF) << (8 * b);
-              }
-              w[q] = outw;
-            }
-            st_v4(rp + g, w);
+            for (int u = 0; u < 16; ++u) acc[q * 16 + u] += __float2int_rn(__uint_as_float(v[u]));
           }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(lead_acce0 + 8 * buf);
         }
+        if (!ok) break;
+        // end of modulus i in this launch: sums mod m_i, added to the residues
+        // of the earlier depth segments
+        const int m = P.crt.m[i];
+        const float inv = P.crt.inv_m[i];
+        const int off = m << 22;  // makes every sum non-negative (|sum| <= 256 x 128 products x 2^14)
+#pragma unroll
+        for (int u = 0; u < 128; ++u) acc[u] = mod_small(acc[u] + off, m, inv);
+        uint4 *rp = res_ptr(i);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          // ordered loads and stores: one 16-byte group of residues in flight at a time
+          uint32_t w[4] = {0u, 0u, 0u, 0u};
+          if (!pr.seg_first) ld_v4(rp + g, w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint32_t outw = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              int r = acc[g * 16 + q * 4 + b] + (int)((w[q] >> (8 * b)) & 0xFFu);
+              r = (r >= m) ? r - m : r;
+              outw |= (uint32_t)r << (8 * b);
+            }
+            w[q] = outw;
+          }
+          st_v4(rp + g, w);
+        }
+      }
       if (!ok) break;
       if (!pr.seg_last) continue;
       // ---- last segment: C' from its residues (CRT), scaled to FP64 by 2^(eA + eB - 2b)
@@ -1944,7 +1958,9 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
     }
     if (ctx->tiles_count == 0) return HSGEN_OK;
     const int nkb_all = (int)(ldk / BK);
-    const int seg_kb = std::max(1, ctx->kseg_blocks);
+    // moduli form: at most 256 k-blocks per launch (32 chunks of exact FP32
+    // sums keep the epilogue's int32 sums below 2^29)
+    const int seg_kb = crt ? std::max(1, std::min(ctx->kseg_blocks, 256)) : std::max(1, ctx->kseg_blocks);
     const long long per = ctx->tiles_count;
     // one launch: the tiles [t0, t0 + cnt) of the list, of H (and S), over
     // the depth segment [kb0, kb0 + seg)
@@ -2116,7 +2132,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   const int nt = (int)ctx->types.size();
   const int uplo = ctx->opt.uplo;
   const int nkb_all = (int)(ldk / BK);
-  const int seg_kb = std::max(1, ctx->kseg_blocks);
+  const int seg_kb = crt ? std::max(1, std::min(ctx->kseg_blocks, 256)) : std::max(1, ctx->kseg_blocks);
   const int nseg = (nkb_all + seg_kb - 1) / seg_kb;
   auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
   // ---- plan: groups of k-points whose slices fit the budget
