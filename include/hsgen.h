@@ -270,8 +270,8 @@ hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
  * 5..7) the smallest count within half of opt.target_rel_err, searched from
  * the a-priori choice; of the two, the faster build on this GPU is kept
  * (hsgen_stats tuned_rel_err reports its error). (2) The schedule: times builds for
- * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 ({32, 48, 64,
- * 96, 128} for the moduli scheme; tile band 16),
+ * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 ({16, 24, 32,
+ * 48, 64} for the moduli scheme; tile band 16),
  * then tile bands {8, 32} with the best segment, then, for the moduli scheme,
  * its kernel's other stage geometry (hsgen_stats stage_geometry). The choices stay in the
  * context for later builds (batched ones use the schedule) and H and S are

@@ -10,7 +10,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -992,9 +991,9 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   double best = 1e300;
   // the moduli kernel sweeps each modulus over the segment before the next
   // one, so its operands stay in L2 only for short segments
-  const std::initializer_list<int> segs = split_plan(ctx, ctx->depth).scheme == kSchemeModuli
-                                               ? std::initializer_list<int>{64, 32, 48, 96, 128}
-                                               : std::initializer_list<int>{128, 64, 96, 192, 256};
+  const std::vector<int> segs = split_plan(ctx, ctx->depth).scheme == kSchemeModuli
+                                    ? std::vector<int>{32, 16, 24, 48, 64}
+                                    : std::vector<int>{128, 64, 96, 192, 256};
   for (int kseg : segs) {
     double ms = 0.0;
     hsgen_status st = trial(kseg, 16, ms);

@@ -735,12 +735,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 // The launch that ends the depth reconstructs C' from the residues (128-bit
 // integers), scales it to FP64 and writes (or adds) the tile of H or S.
 constexpr int BNC = 128;  // complex output columns of a moduli-form tile
-// stage geometries of the moduli kernel: (k-blocks per stage, stages, k-blocks
-// per accumulation chunk); a chunk holds at most 1024 products (exact in FP32)
-struct CrtGeom {
-  int kps, nst, ckb;
-};
-constexpr CrtGeom kCrtGeoms[2] = {{2, 3, 8}, {3, 2, 6}};
+// the moduli kernel's stage geometries, as template arguments (k-blocks per
+// stage, stages, k-blocks per accumulation chunk): <2, 3, 8> and <3, 2, 6>; a
+// chunk holds at most 1024 products (exact in FP32)
 
 __device__ __forceinline__ Tile decode_tile_crt(const GemmParams &P, long long t, long long &slot) {
   int pi = 0, hi = P.nprob;
