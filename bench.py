@@ -125,22 +125,29 @@ class ClockSampler:
         return out
 
 
-def _traffic(config: int):
-    """DRAM bytes per H/S launch of the split kernel from the committed ncu record,
-    or None when the record is for another workload or the kernel source changed."""
+def _traffic(config: int, kseg: int, scheme: int):
+    """DRAM bytes per H/S depth-segment launch of the moduli kernel from the
+    committed ncu record, or None when the record is for another workload,
+    schedule or form, or the kernel's source has changed since."""
     import hashlib
 
     here = os.path.dirname(os.path.abspath(__file__))
     try:
-        with open(os.path.join(here, "profiles", "split_gemm_dram_traffic_256atoms_NG20000.json")) as f:
+        with open(os.path.join(here, "profiles", "crt_gemm_dram_traffic_256atoms_NG20000.json")) as f:
             rec = json.load(f)
-        with open(os.path.join(here, "paper_1602_06589_gb300", "csrc", "split.cu"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        with open(os.path.join(here, "paper_1602_06589_gb300", "csrc", "split.cu")) as f:
+            src = f.read()
     except OSError:
         return None
-    if config != 4 or rec.get("kernel_source_sha256") != sha:
+    try:
+        a = src.index("template <int KPS_, int NST_, int CKB_>")
+        b = src.index("// ---------------------------------------------------------------------------\n// Slicing kernel")
+    except ValueError:
         return None
-    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    sha = hashlib.sha256(src[a:b].encode()).hexdigest()
+    if config != 4 or kseg != 32 or scheme != 2 or rec.get("kernel_source_sha256") != sha:
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"], rec["algorithmic_bytes"]
 
 
 # whole columns of the triangle compared with the oracle after the timed
@@ -594,13 +601,17 @@ def roofline(st, f_contract, c_ms, precision, peaks, clk_s, args, hsgen):
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         pmhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
         peak_clk = peak * mhz / pmhz if (mhz and pmhz) else peak
+        tr = _traffic(args.config, st.get("kseg_blocks", 0), scheme) \
+            if not args.n_g and st.get("s_form") != hsgen.S_LEGENDRE else None
         return {"bound": "tensor", "achieved": achieved, "peak": peak_clk, "unit": "TFLOP/s",
                 "frac": achieved / peak_clk, "frac_vs_measured_peak": achieved / peak,
                 "measured_peak": peak, "measured_peak_mhz": pmhz, "run_mhz": mhz,
                 "bf16_products_per_fp64_mac": units,
-                "traffic": _traffic(args.config) if not args.n_g and st.get("s_form") != hsgen.S_LEGENDRE else None,
+                "traffic": tr[0] if tr else None,
                 "traffic_unit": "DRAM bytes per H/S depth-segment launch (ncu, 1 pass)",
-                "kernel": "split H/S contraction (tcgen05 bf16)",
+                "traffic_algorithmic_bytes": tr[1] if tr else None,
+                "kernel": ("H/S contraction, moduli scheme (crt_gemm_kernel, tcgen05 bf16)" if scheme == 2 else
+                           "H/S contraction, slices scheme (split_gemm_kernel, tcgen05 bf16)"),
                 "peak_source": ("measured bf16 sustained (MEASURED_PEAKS.json), scaled to the sampled SM clock"
                                 if "bf16_tflops_sustained" in peaks else "fallback")}
     achieved = f_contract / (c_ms * 1e-3) / 1e12

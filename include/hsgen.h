@@ -44,8 +44,8 @@
  * by hsgen_create; hsgen_autotune picks them per shape); HSGEN_WS_BYTES, the
  * split form's workspace budget that sets the passes over the atoms when
  * opt.atom_chunk is 0 (default 176e9); HSGEN_BATCH_BYTES,
- * the slice-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
- * block rows of the split-form hsgen_reduce_generalized (default 256).
+ * the operand-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
+ * block rows of hsgen_reduce_generalized (default 128).
  * Fault injection (tests): HSGEN_FAIL_ALLOC=1 makes every growth of a
  * library workspace fail as an out-of-memory cudaMalloc would (the call
  * returns HSGEN_ENOMEM; the context stays usable once the variable is unset).
@@ -220,8 +220,12 @@ hsgen_status hsgen_build_HS_blocks(hsgen_ctx *ctx, int n_g, const double *kvec, 
 
 /* Builds H and S for n_k k-points in one go (one H, S per k-point, Sec. 2.3):
  * n_g[k], kvec[k] (host pointers to [n_g[k]][3]), H[k], S[k] device
- * pointers with leading dimension ld[k]. All k-points' contraction tiles run
- * in one persistent launch over a grouped tile queue. */
+ * pointers with leading dimension ld[k]. The whole kernel sequence is
+ * captured in a CUDA graph and replayed while sizes and pointers stay the
+ * same. Slices scheme: the contraction tiles of a group of k-points (up to
+ * HSGEN_BATCH_BYTES of operand planes, default 96 GiB) run in one persistent
+ * launch over a grouped tile queue; moduli scheme: one k-point per group.
+ * The FP64 form loops over hsgen_build_HS. */
 hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec,
                                     void *const *H, void *const *S, const long long *ld, void *cuda_stream);
 

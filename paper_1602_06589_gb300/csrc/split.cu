@@ -769,15 +769,6 @@ __device__ __forceinline__ void st_v4(uint4 *p, const uint32_t (&w)[4]) {
                : "memory");
 }
 
-// a mod m for 0 <= a < 2^26, 2 <= m <= 256: the truncated float quotient
-// is within one of the true one (the roundings of a, of 1/m and of the
-// product move a / m by less than 0.05), so one correction each way suffices
-__device__ __forceinline__ int mod_small26(int a, int m, float inv_m) {
-  const int q = __float2int_rz(__int2float_rz(a) * inv_m);
-  int r = a - q * m;
-  r = (r < 0) ? r + m : r;
-  return (r >= m) ? r - m : r;
-}
 
 // a mod m for 0 <= a < 2^31, 2 <= m <= 256: the float quotient is within 3
 // of the true one (rounding of a, of 1/m and of the product), then corrected
@@ -1162,11 +1153,13 @@ __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ 
 // Moduli form: residues of the b-bit integers N = round(v 2^(b - e)) (one
 // scale 2^e per column) for every modulus, balanced to |r| <= 128, as BF16
 // planes in the k-blocked layout of slice_kernel; plane i * planes + {0, 1, 2}
-// holds re, im, -re of modulus i. |N| < 2^48 is cut into three 16-bit pieces,
-// so |N| mod m = (p2 (2^32 mod m) + p1 (2^16 mod m) + p0) mod m with 32-bit
-// integer arithmetic only. Each thread takes two consecutive depth rows (one
-// 4-byte store per plane).
-__constant__ int c_pow16[kMaxModuli][2];  // 2^16 mod m_i, 2^32 mod m_i
+// holds re, im, -re of modulus i. |N| < 2^48 is cut into four 12-bit pieces,
+// exact in FP32, so |N| mod m = sum_j piece_j (2^12j mod m) mod m is formed
+// in FP32 (every partial sum is an integer below 2^22, exact) with a
+// quotient rounded by the 1.5 2^23 shift: full-rate FP32 work, no integer
+// division and no conversion instruction. Each thread takes two consecutive
+// depth rows (one 4-byte store per plane).
+__constant__ float c_pow12[kMaxModuli][3];  // 2^12, 2^24, 2^36 mod m_i
 
 __global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict__ src, long long lds, int K,
                                                       const double *__restrict__ urow, int b, CrtConsts crt,
@@ -1195,9 +1188,10 @@ __global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict_
   }
   __syncthreads();
   const int shift = b - e_sh;
+  constexpr float kShift = 12582912.0f;  // 1.5 2^23: adding and subtracting it rounds to an integer
   for (int k = 2 * threadIdx.x; k < (int)ldk; k += 2 * blockDim.x) {  // ldk is a multiple of 64
-    // (row, re/im): magnitude pieces and sign
-    int p0[4], p1[4], p2[4];
+    // (row, re/im): |N| in four exact FP32 pieces, and the sign
+    float pc[4][4];
     bool ng[4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -1217,26 +1211,30 @@ __global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict_
         const int q = 2 * z + h;
         ng[q] = N[z] < 0;
         const unsigned long long a = ng[q] ? (unsigned long long)(-N[z]) : (unsigned long long)N[z];
-        p0[q] = (int)(a & 0xFFFFu);
-        p1[q] = (int)((a >> 16) & 0xFFFFu);
-        p2[q] = (int)(a >> 32);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          pc[q][j] = __int_as_float(0x4B000000 | (int)((a >> (12 * j)) & 0xFFFu)) - 8388608.0f;
       }
     }
     __nv_bfloat16 *out = dst + ((size_t)(k >> 6) * ncols + col) * 64 + (k & 63);
     for (int i = 0; i < crt.n; ++i) {
-      const int m = crt.m[i];
-      const int c16 = c_pow16[i][0], c32 = c_pow16[i][1];
+      const float m = (float)crt.m[i], inv = crt.inv_m[i], half = 0.5f * m;
+      const float c12 = c_pow12[i][0], c24 = c_pow12[i][1], c36 = c_pow12[i][2];
       float r[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        int x = mod_small26(p2[q] * c32 + p1[q] * c16 + p0[q], m, crt.inv_m[i]);  // |N| mod m (< 2^25 in)
-        if (ng[q] && x) x = m - x;                                              // N mod m
-        r[q] = (float)((2 * x > m) ? x - m : x);                                // balanced, |r| <= 128
+        const float a = __fmaf_rn(pc[q][3], c36, __fmaf_rn(pc[q][2], c24, __fmaf_rn(pc[q][1], c12, pc[q][0])));
+        const float qt = __fmaf_rn(a, inv, kShift) - kShift;  // a / m rounded, within one of the floor
+        float x = __fmaf_rn(-qt, m, a);                       // |N| mod m, up to one m off: |x| < 0.51 m
+        x = ng[q] ? -x : x;                                    // N mod m, up to one m off
+        x = (x > half) ? x - m : x;                            // balanced: |x| <= m / 2 <= 128
+        r[q] = (x < -half) ? x + m : x;
       }
       __nv_bfloat162 *base = (__nv_bfloat162 *)(out + (size_t)i * planes * plane_stride);
       base[0] = __floats2bfloat162_rn(r[0], r[1]);  // re of rows k, k + 1
       *(__nv_bfloat162 *)((__nv_bfloat16 *)base + plane_stride) = __floats2bfloat162_rn(r[2], r[3]);
-      if (planes == 3) *(__nv_bfloat162 *)((__nv_bfloat16 *)base + 2 * plane_stride) = __floats2bfloat162_rn(-r[0], -r[1]);
+      if (planes == 3)
+        *(__nv_bfloat162 *)((__nv_bfloat16 *)base + 2 * plane_stride) = __floats2bfloat162_rn(-r[0], -r[1]);
     }
   }
 }
@@ -1425,15 +1423,14 @@ CrtConsts make_crt(int n) {
   return c;
 }
 
-// 2^16 and 2^32 mod m_i for the residue kernel (constant memory, once per device)
+// 2^12, 2^24 and 2^36 mod m_i for the residue kernel (constant memory, once per device)
 cudaError_t upload_crt_table() {
-  int tab[kMaxModuli][2];
+  float tab[kMaxModuli][3];
   for (int i = 0; i < kMaxModuli; ++i) {
     const long long m = kModuli[i];
-    tab[i][0] = (int)((1LL << 16) % m);
-    tab[i][1] = (int)((1LL << 32) % m);
+    for (int j = 0; j < 3; ++j) tab[i][j] = (float)((1LL << (12 * (j + 1))) % m);
   }
-  return cudaMemcpyToSymbol(c_pow16, tab, sizeof(tab));
+  return cudaMemcpyToSymbol(c_pow12, tab, sizeof(tab));
 }
 
 cudaError_t launch_slice(const double2 *src, long long lds, int K, const double *urow, int s, int planes,
@@ -2133,7 +2130,10 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   const int nseg = (nkb_all + seg_kb - 1) / seg_kb;
   auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
   // ---- plan: groups of k-points whose slices fit the budget
-  size_t budget = (size_t)96 << 30;
+  // slices: groups of k-points up to 96 GiB of planes share each launch;
+  // moduli: one k-point per group (grouping measured slower at N_G ~3300:
+  // 8.5 ms per k-point against 7.8 for one k-point per launch)
+  size_t budget = crt ? 1 : (size_t)96 << 30;
   if (const char *e = std::getenv("HSGEN_BATCH_BYTES")) budget = (size_t)std::max(1.0, std::atof(e));
   // per k-point: 8 planes per slice or modulus (W 3, X 3, U W 2), and in the
   // moduli form its residue store (H and S tiles)
