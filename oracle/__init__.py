@@ -13,6 +13,8 @@ from .hsref import (  # noqa: F401
     wigner3j,
     gaunt,
     T_matrix,
+    cholesky,
+    T_hpd_info,
     coefficients,
     build_HS,
     HS_entries,

@@ -236,6 +236,43 @@ int hsref_T(const hsref_type *ty, double *T) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* HPD test of a species' T (Sec. 4.6.2-4.6.3, Listings alg:H_AA_HPD and    */
+/* alg:H_AA_dynamic): the Cholesky factorisation T = C C^H (C lower         */
+/* triangular, real positive diagonal) attempted column by column, reading  */
+/* the lower triangle of T only. The status follows LAPACK potrf, whose     */
+/* error code the paper branches on: 0 when every pivot is positive (T is   */
+/* HPD and C its factor); k > 0 when the k-th pivot is not positive or not  */
+/* finite, i.e. the leading minor of order k is not positive definite.     */
+/* ------------------------------------------------------------------------ */
+int hsref_cholesky(int n, const double *T, long long ld, double *C) {
+  const double complex *A = (const double complex *)T;
+  double complex *L = (double complex *)calloc((size_t)n * n + 1, sizeof(double complex));
+  if (!L) return -1;
+  int info = 0;
+  for (int j = 0; j < n && !info; ++j) {
+    double d = creal(A[j + (size_t)j * ld]);
+    for (int k = 0; k < j; ++k) {
+      double complex c = L[j + (size_t)k * n];
+      d -= creal(c) * creal(c) + cimag(c) * cimag(c);
+    }
+    if (!(d > 0.0) || !isfinite(d)) {
+      info = j + 1;
+      break;
+    }
+    const double cjj = sqrt(d);
+    L[j + (size_t)j * n] = cjj;
+    for (int i = j + 1; i < n; ++i) {
+      double complex v = A[i + (size_t)j * ld];
+      for (int k = 0; k < j; ++k) v -= L[i + (size_t)k * n] * conj(L[j + (size_t)k * n]);
+      L[i + (size_t)j * n] = v / cjj;
+    }
+  }
+  if (C) memcpy(C, L, sizeof(double complex) * (size_t)n * n);
+  free(L);
+  return info;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Matching coefficients, Eqs. def_a_tensor / def_b_tensor:                 */
 /*  A_{L,a,t} = 4 pi/(W_l sqrt(Omega)) i^l e^{i K_t.x_a} Y*_L(R_a K^_t)     */
 /*              [u_dot K j_l'(R K) - u_dot' j_l(R K)]                        */

@@ -61,6 +61,12 @@ double hsref_wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
 double hsref_gaunt(int l, int m, int lp, int mp, int lpp, int mpp);
 /* T = [[T^AA, T^AB], [T^BA, T^BB]] (2N_L x 2N_L, column-major) (Eq. t_matrices). */
 int hsref_T(const hsref_type *ty, double *T);
+/* Cholesky factorisation T = C C^H of an n x n Hermitian matrix (lower
+ * triangle of T read, leading dimension ld; C: n x n, column-major, lower,
+ * or NULL). Returns 0 (T is HPD) or k > 0, the order of the first leading
+ * minor that is not positive definite (the status of LAPACK potrf); -1 when
+ * out of memory. Sec. 4.6.2-4.6.3: the HPD test that routes a species. */
+int hsref_cholesky(int n, const double *T, long long ld, double *C);
 /* W_a = [A_a; B_a]: out[t][2N_L] (column t contiguous) (Eqs. def_a_tensor/def_b_tensor). */
 int hsref_coefficients(const hsref_system *sys, int atom, int n_g, const double *kvec, double *W);
 /* Full H and S (column-major, leading dimension ld). full=0: upper triangle

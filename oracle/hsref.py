@@ -43,6 +43,7 @@ def _bind(path: str):
     lib.hsref_gaunt.argtypes = [C.c_int] * 6
     lib.hsref_gaunt.restype = C.c_double
     lib.hsref_T.argtypes = [C.POINTER(_Type), _dp]
+    lib.hsref_cholesky.argtypes = [C.c_int, _dp, C.c_longlong, _dp]
     lib.hsref_coefficients.argtypes = [C.POINTER(_System), C.c_int, C.c_int, _dp, _dp]
     lib.hsref_build_HS.argtypes = [C.POINTER(_System), C.c_int, _dp, _dp, _dp, C.c_longlong, C.c_int, C.c_int]
     lib.hsref_HS_entries.argtypes = [C.POINTER(_System), C.c_int, _dp, C.c_int, _ip, _ip, _dp, _dp, C.c_int]
@@ -164,6 +165,26 @@ def T_matrix(atom_type) -> np.ndarray:
     if load().hsref_T(C.byref(m.types[0]), _d(out)) != 0:
         raise RuntimeError("hsref_T failed")
     return out.view(np.complex128).reshape(n, n, order="F")
+
+
+def cholesky(T: np.ndarray):
+    """(info, C): the Cholesky factor C (lower, C C^H = T) of a Hermitian T
+    and the potrf-style status (0: HPD; k > 0: the leading minor of order k
+    is not positive definite, C then holds the first k - 1 columns)."""
+    A = _c128(T)
+    n = A.shape[0]
+    buf = _c128(A.reshape(-1, order="F")).view(np.float64).copy()
+    out = np.zeros(2 * n * n)
+    info = load().hsref_cholesky(n, _d(buf), max(n, 1), _d(out))
+    if info < 0:
+        raise MemoryError("hsref_cholesky")
+    return int(info), out.view(np.complex128).reshape(n, n, order="F")
+
+
+def T_hpd_info(atom_type) -> int:
+    """Sec. 4.6.3: the status of the Cholesky factorisation of the species'
+    T (0: HPD, the species takes the H = Y^H Y route)."""
+    return cholesky(T_matrix(atom_type))[0]
 
 
 def coefficients(sysm, atom: int, kvec: np.ndarray) -> np.ndarray:

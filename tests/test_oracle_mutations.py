@@ -15,6 +15,7 @@ import pytest
 import oracle
 from oracle import hsref as _hsref
 
+import test_oracle_hpd as Hp
 import test_oracle_physics as P
 import test_oracle_special as Sp
 
@@ -67,6 +68,13 @@ MUTATIONS = {
         "Sc[e] = cdot(w + (size_t)tp * D, x + (size_t)c * D, D, 0);"),
     "l_nonsph cutoff on one index only": (
         "lpp <= l + lp && l <= lns && lp <= lns; ++lpp", "lpp <= l + lp && l <= lns; ++lpp"),
+    "Cholesky pivot with c^2 instead of |c|^2": (
+        "d -= creal(c) * creal(c) + cimag(c) * cimag(c);", "d -= creal(c * c);"),
+    "Cholesky conjugate on the wrong factor": (
+        "v -= L[i + (size_t)k * n] * conj(L[j + (size_t)k * n]);",
+        "v -= conj(L[i + (size_t)k * n]) * L[j + (size_t)k * n];"),
+    "Cholesky pivot test admits zero": (
+        "if (!(d > 0.0) || !isfinite(d)) {", "if (!(d >= 0.0) || !isfinite(d)) {"),
     "conjugate on the wrong side of the dot": (
         "sr += pr * qr + pi * qi;\n      si += pr * qi - pi * qr;",
         "sr += pr * qr + pi * qi;\n      si += pi * qr - pr * qi;"),
@@ -88,6 +96,10 @@ PINS = [
     lambda: P.test_invariances(),
     lambda: P.test_caller_wronskian(),
     lambda: P.test_whole_columns_match_full_matrix(),
+    lambda: Hp.test_factor_of_hpd_matrix(7),
+    lambda: Hp.test_special_cases(),
+    lambda: [Hp.test_status_is_the_first_indefinite_leading_minor(k) for k in range(6)],
+    lambda: Hp.test_energy_shift_adds_sigma_D_and_makes_T_hpd(),
 ]
 
 

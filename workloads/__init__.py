@@ -13,5 +13,6 @@ from .synth import (  # noqa: F401
     make_system,
     kpoint_list,
     reciprocal,
+    shift_energies,
     CONFIG_NAMES,
 )

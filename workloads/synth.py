@@ -25,7 +25,7 @@ smallest |K_t|, ties broken by the integer triple of G (Sec. 2.2).
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -268,3 +268,15 @@ def make_config(index: int, n_g_override: Optional[int] = None) -> Workload:
     else:
         raise ValueError(f"no config {index}")
     return Workload(CONFIG_NAMES[index], sysm, ks)
+
+
+def shift_energies(sysm: System, sigma: float, types: Optional[Sequence[int]] = None) -> System:
+    """The same system with every E_l of the chosen species (default: all)
+    raised by sigma, a shift of the energy reference. It turns the species'
+    T positive definite once sigma is large enough, the case of Sec. 4.6.2
+    (the stand-in radial data draw E_l from [-1, 1], so no species is HPD
+    as drawn). Species with a T_override are left as they are."""
+    chosen = set(range(len(sysm.types)) if types is None else (int(t) for t in types))
+    new = [replace(ty, e_l=ty.e_l + sigma) if (i in chosen and ty.T_override is None) else ty
+           for i, ty in enumerate(sysm.types)]
+    return replace(sysm, types=new)
