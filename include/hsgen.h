@@ -40,8 +40,9 @@
  * Buffers on another GPU than the context's are rejected (HSGEN_EINVAL).
  * Environment (tuning only; results move at the rounding level at most):
  * HSGEN_KSEG_BLOCKS, the split form's depth segment in 64-deep blocks, and
- * HSGEN_CRT_GEOMETRY (0 or 1), the moduli kernel's stage geometry (both read
- * by hsgen_create; hsgen_autotune picks them per shape); HSGEN_WS_BYTES, the
+ * HSGEN_CRT_GEOMETRY (0 or 1), the moduli kernel's stage geometry, and
+ * HSGEN_CRT_ORDER (0 or 1), the order of its work units (all read by
+ * hsgen_create; hsgen_autotune picks them per shape); HSGEN_WS_BYTES, the
  * split form's workspace budget that sets the passes over the atoms when
  * opt.atom_chunk is 0 (default 176e9); HSGEN_BATCH_BYTES,
  * the operand-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
@@ -162,6 +163,10 @@ typedef struct {
                            /* measured)                                         */
   int stage_geometry;      /* moduli scheme: pipeline stages of its kernel, 0:  */
                            /* three of two 64-deep blocks, 1: two of three      */
+  int unit_order;          /* moduli scheme: order of its (tile, modulus) work  */
+                           /* units, 0: every modulus of a tile before the next */
+                           /* tile, 1: every tile of a modulus before the next  */
+                           /* modulus                                           */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -274,13 +279,14 @@ hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
  * 5..7) the smallest count within half of opt.target_rel_err, searched from
  * the a-priori choice; of the two, the faster build on this GPU is kept
  * (hsgen_stats tuned_rel_err reports its error). (2) The schedule: times builds for
- * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 ({16, 24, 32,
- * 48, 64} for the moduli scheme; tile band 16),
- * then tile bands {8, 32} with the best segment, then, for the moduli scheme,
- * its kernel's other stage geometry (hsgen_stats stage_geometry). The choices stay in the
+ * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 (moduli scheme:
+ * {16, 32, 64, 128} in modulus-major unit order and {16, 24, 32, 48, 64} in
+ * tile-major order; tile band 16), then tile bands {8, 32, 64} with the best
+ * segment, then, for the moduli scheme, its kernel's other stage geometry
+ * (hsgen_stats unit_order, stage_geometry). The choices stay in the
  * context for later builds (batched ones use the schedule) and H and S are
  * left built with them. Same arguments as hsgen_build_HS; synchronous; about
- * ten to fifteen builds long. The FP64 form has nothing to tune: it builds
+ * ten to twenty builds long. The FP64 form has nothing to tune: it builds
  * once and returns HSGEN_OK. */
 hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);
@@ -295,11 +301,13 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
  * S's opt.uplo triangle becomes the Cholesky factor (U with S = U^H U for
  * 'U', L with S = L L^H for 'L'; the other triangle is left as it was) and H
  * becomes H~ = U^-H H U^-1 (= L^-1 H L^-H), written in full and exactly
- * Hermitian, so that H~ y = eps y and c = U^-1 y (= L^-H y). With
- * opt.precision HSGEN_SPLIT and the upper triangle the factorization and the
- * two triangular solves run blocked (256 rows; FP64 diagonal blocks, the
- * updates as 7-slice BF16 products on the tensor cores, to FP64-level
- * accuracy); otherwise cuSOLVER ZPOTRF and cuBLAS ZTRSM in FP64. Runs on
+ * Hermitian, so that H~ y = eps y and c = U^-1 y (= L^-H y). Everything
+ * runs in the library's own kernels, blocked by HSGEN_REDUCE_BLOCK rows
+ * (default 128): the diagonal blocks' Cholesky factors and inverses in FP64
+ * tile kernels; the panel and trailing updates and the two triangular solves
+ * as products with those inverses, 7-slice BF16 products on the tensor cores
+ * with opt.precision HSGEN_SPLIT (FP64-level accuracy) or FP64 DMMA products
+ * otherwise; the lower layout works on a conjugate-transposed copy. Runs on
  * `cuda_stream` and returns when it is done. HSGEN_ENUMERIC when S is not
  * positive definite: the leading minor that failed is named in
  * hsgen_last_error, and H and S are then overwritten with partial results
