@@ -41,8 +41,9 @@
  * Environment (tuning only; results move at the rounding level at most):
  * HSGEN_KSEG_BLOCKS, the split form's depth segment in 64-deep blocks, and
  * HSGEN_CRT_GEOMETRY (0 or 1), the moduli kernel's stage geometry, and
- * HSGEN_CRT_ORDER (0 or 1), the order of its work units (all read by
- * hsgen_create; hsgen_autotune picks them per shape); HSGEN_WS_BYTES, the
+ * HSGEN_CRT_ORDER (0 or 1), the order of its work units, and
+ * HSGEN_TILE_BAND, the split form's tile band in 64-column blocks (all read
+ * by hsgen_create; hsgen_autotune picks them per shape); HSGEN_WS_BYTES, the
  * split form's workspace budget that sets the passes over the atoms when
  * opt.atom_chunk is 0 (default 176e9); HSGEN_BATCH_BYTES,
  * the operand-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
@@ -280,13 +281,13 @@ hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
  * the a-priori choice; of the two, the faster build on this GPU is kept
  * (hsgen_stats tuned_rel_err reports its error). (2) The schedule: times builds for
  * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 (moduli scheme:
- * {16, 32, 64, 128} in modulus-major unit order and {16, 24, 32, 48, 64} in
- * tile-major order; tile band 16), then tile bands {8, 32, 64} with the best
- * segment, then, for the moduli scheme, its kernel's other stage geometry
+ * {64, 128, 256} in modulus-major unit order and 32 in tile-major order;
+ * tile band 16), then tile bands {8, 32} with the best segment, then, for
+ * the moduli scheme, its kernel's other stage geometry
  * (hsgen_stats unit_order, stage_geometry). The choices stay in the
  * context for later builds (batched ones use the schedule) and H and S are
  * left built with them. Same arguments as hsgen_build_HS; synchronous; about
- * ten to twenty builds long. The FP64 form has nothing to tune: it builds
+ * ten to fifteen builds long. The FP64 form has nothing to tune: it builds
  * once and returns HSGEN_OK. */
 hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H, void *S, long long ld,
                             void *cuda_stream);

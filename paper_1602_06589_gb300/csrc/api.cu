@@ -211,6 +211,8 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   ctx->opt = o;
   if (const char *ks = std::getenv("HSGEN_KSEG_BLOCKS")) ctx->kseg_blocks = std::max(1, std::atoi(ks));
   if (const char *cg = std::getenv("HSGEN_CRT_GEOMETRY")) ctx->crt_geom = std::atoi(cg) == 1 ? 1 : 0;
+  if (const char *co = std::getenv("HSGEN_CRT_ORDER")) ctx->crt_order = std::atoi(co) == 1 ? 1 : 0;
+  if (const char *tb = std::getenv("HSGEN_TILE_BAND")) ctx->tile_band = std::max(1, std::atoi(tb));
   if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess ||
       split_upload_tables() != cudaSuccess) {
     delete ctx;
@@ -989,21 +991,34 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   };
   int best_k = ctx->kseg_blocks, best_b = ctx->tile_band;
   double best = 1e300;
-  // the moduli kernel sweeps each modulus over the segment before the next
-  // one, so its operands stay in L2 only for short segments
-  const std::vector<int> segs = split_plan(ctx, ctx->depth).scheme == kSchemeModuli
-                                    ? std::vector<int>{32, 16, 24, 48, 64}
-                                    : std::vector<int>{128, 64, 96, 192, 256};
-  for (int kseg : segs) {
+  const bool moduli = split_plan(ctx, ctx->depth).scheme == kSchemeModuli;
+  // (order, segment) candidates. Slices: one order. Moduli, tile-major order:
+  // each modulus is swept over the segment before the next one, so a wave's
+  // operands stay in L2 only for short segments; modulus-major order: a
+  // column band's operand blocks of one modulus stay in L2 while the waves
+  // sweep its rows, which allows longer segments (fewer passes over the
+  // residue store).
+  std::vector<std::pair<int, int>> cands;
+  if (moduli) {
+    for (int k : {128, 64, 256}) cands.push_back({1, k});
+    cands.push_back({0, 32});
+  } else {
+    for (int k : {128, 64, 96, 192, 256}) cands.push_back({ctx->crt_order, k});
+  }
+  int best_o = ctx->crt_order;
+  for (const auto &c : cands) {
+    ctx->crt_order = c.first;
     double ms = 0.0;
-    hsgen_status st = trial(kseg, 16, ms);
+    hsgen_status st = trial(c.second, 16, ms);
     if (st != HSGEN_OK) return st;
     if (ms < best) {
       best = ms;
-      best_k = kseg;
+      best_o = c.first;
+      best_k = c.second;
       best_b = 16;
     }
   }
+  ctx->crt_order = best_o;
   for (int band : {8, 32}) {
     double ms = 0.0;
     hsgen_status st = trial(best_k, band, ms);
@@ -1068,6 +1083,7 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   st.kseg_blocks = ctx->kseg_blocks;
   st.tile_band = ctx->tile_band;
   st.stage_geometry = ctx->crt_geom;
+  st.unit_order = ctx->crt_order;
   *out = st;
   // the stats are filled in either way; a wait that expired is reported here
   return split_poll_status(ctx, true);

@@ -144,6 +144,7 @@ struct GemmParams {
   int *status;
   unsigned long long timeout_ns;
   CrtConsts crt;  // moduli form only
+  int crt_order;  // moduli form: 0 tile-major units, 1 modulus-major (see crt_unit)
 };
 
 // ---------------------------------------------------------------------------
@@ -764,6 +765,10 @@ __device__ __forceinline__ void ld_v4(const uint4 *p, uint32_t (&w)[4]) {
   asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p)
                : "memory");
 }
+// Asynchronous prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void st_v4(uint4 *p, const uint32_t (&w)[4]) {
   asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
                : "memory");
@@ -781,6 +786,28 @@ __device__ __forceinline__ int mod_small(int a, int m, float inv_m) {
     r = (r >= m) ? r - m : r;
   }
   return r;
+}
+
+// The work of a CTA pair is its tiles t = pair, pair + npairs, .. times the
+// n moduli, in units (modulus i, tile t). Tile-major order (0) runs every
+// modulus of a tile before its next tile, so the operands a wave of tiles
+// shares are fetched again for every modulus; modulus-major order (1) runs all
+// of the pair's tiles for modulus 0, then for modulus 1, .., so consecutive
+// waves of the grid work on one modulus and share its operand blocks in L2.
+// Either way the last unit of a tile is its last modulus, where the launch
+// that ends the depth reconstructs the tile from the residues the same
+// threads stored for the earlier moduli.
+__device__ __forceinline__ void crt_unit(long long u, int nm, long long my_tiles, long long pair, long long npairs,
+                                         int order, int &i, long long &t) {
+  long long k;
+  if (order == 1) {
+    i = (int)(u / my_tiles);
+    k = u - (long long)i * my_tiles;
+  } else {
+    k = u / nm;
+    i = (int)(u - k * nm);
+  }
+  t = pair + k * npairs;
 }
 
 template <int KPS_, int NST_, int CKB_>
@@ -805,6 +832,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
   const uint32_t lead_full0 = map_rank(full0, 0), lead_acce0 = map_rank(acce0, 0);
   const long long pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
   const int NM = P.crt.n;
+  const long long my_tiles = P.ntiles > pair ? (P.ntiles - 1 - pair) / npairs + 1 : 0;
+  const long long nunits = my_tiles * NM;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NST; ++i) {
@@ -834,39 +863,40 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // ------------------------------ TMA producer ------------------------------
     uint32_t it = 0;
     bool ok = true;
-    for (long long t = pair; t < P.ntiles && ok; t += npairs) {
-      long long slot;
+    for (long long un = 0; un < nunits && ok; ++un) {
+      int i;
+      long long t, slot;
+      crt_unit(un, NM, my_tiles, pair, npairs, P.crt_order, i, t);
       const Tile ti = decode_tile_crt(P, t, slot);
       const GemmProblem &pr = problem(P, ti.prob);
       const CUtensorMap *mA = map_a(P, ti.prob), *mB = map_b(P, ti.prob);
-      for (int i = 0; i < NM && ok; ++i)
-        for (int kb = 0; kb < ti.nkb && ok; kb += KPS) {
-          const int nk = min(KPS, ti.nkb - kb);
-          const uint32_t bytes = nk * 2 * (A_BYTES + B_BYTES);
-          for (int h = 0; h < 2; ++h, ++it) {
-            const int st = it % NST;
-            const uint32_t round = it / NST;
-            if (!warp_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
-              if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
-              ok = false;
-              break;
-            }
-            const uint32_t sA0 = sbase + st * STAGE_BYTES;
-            const uint32_t mbar = lead_full0 + 8 * st;
-            const int pa = i * pr.a_pps + h;
-            // B rows [0, 128) in CTA 0, [128, 256) in CTA 1: [re | im] (h = 0), [im | -re] (h = 1)
-            const int pb = i * pr.b_pps + h + (int)rank;
-            const int kbA = pr.kb_begin + kb;
-            if (elect_one()) {
-              if (leader) mbar_expect_tx(full0 + 8 * st, bytes);
-              for (int j = 0; j < nk; ++j) {
-                tma_load_3d(sA0 + j * A_BYTES, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA + j);
-                tma_load_3d(sA0 + STAGE_A + j * B_BYTES, mB, mbar, 0, ti.n0, pb * pr.b_nkb + kbA + j);
-              }
-            }
-            __syncwarp();
+      for (int kb = 0; kb < ti.nkb && ok; kb += KPS) {
+        const int nk = min(KPS, ti.nkb - kb);
+        const uint32_t bytes = nk * 2 * (A_BYTES + B_BYTES);
+        for (int h = 0; h < 2; ++h, ++it) {
+          const int st = it % NST;
+          const uint32_t round = it / NST;
+          if (!warp_wait(empty0 + 8 * st, (round & 1) ^ 1, tmo)) {
+            if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_PRODUCER);
+            ok = false;
+            break;
           }
+          const uint32_t sA0 = sbase + st * STAGE_BYTES;
+          const uint32_t mbar = lead_full0 + 8 * st;
+          const int pa = i * pr.a_pps + h;
+          // B rows [0, 128) in CTA 0, [128, 256) in CTA 1: [re | im] (h = 0), [im | -re] (h = 1)
+          const int pb = i * pr.b_pps + h + (int)rank;
+          const int kbA = pr.kb_begin + kb;
+          if (elect_one()) {
+            if (leader) mbar_expect_tx(full0 + 8 * st, bytes);
+            for (int j = 0; j < nk; ++j) {
+              tma_load_3d(sA0 + j * A_BYTES, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA + j);
+              tma_load_3d(sA0 + STAGE_A + j * B_BYTES, mB, mbar, 0, ti.n0, pb * pr.b_nkb + kbA + j);
+            }
+          }
+          __syncwarp();
         }
+      }
     }
     for (int st = 0; st < NST && leader; ++st) {
       if (it <= (uint32_t)st) break;
@@ -880,52 +910,54 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const uint64_t descA0 = desc_sw128(sbase), descB0 = desc_sw128(sbase + STAGE_A);
       uint32_t it = 0, cc = 0;
       bool ok = true;
-      for (long long t = pair; t < P.ntiles && ok; t += npairs) {
-        long long slot;
+      for (long long un = 0; un < nunits && ok; ++un) {
+        int i;
+        long long t, slot;
+        crt_unit(un, NM, my_tiles, pair, npairs, P.crt_order, i, t);
+        (void)i;
         const Tile ti = decode_tile_crt(P, t, slot);
-        for (int i = 0; i < NM && ok; ++i)
-          for (int kc0 = 0; kc0 < ti.nkb && ok; kc0 += CKB, ++cc) {
-            const int kc1 = min(ti.nkb, kc0 + CKB);
-            const int buf = cc % NACC;
-            const uint32_t use = cc / NACC;
-            if (!warp_wait<true>(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
-              if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t dacc = tbase + buf * 256;
-            uint32_t accum = 0;
-            for (int kb = kc0; kb < kc1 && ok; kb += KPS) {
-              const int nk = min(KPS, kc1 - kb);
-              for (int h = 0; h < 2; ++h, ++it) {
-                const int st = it % NST;
-                if (!warp_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
-                  if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
-                  ok = false;
-                  break;
-                }
-                tc_fence_after();
-                const uint64_t da = descA0 + (uint64_t)(st * (STAGE_BYTES >> 4));
-                const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4));
-                if (elect_one()) {
-                  for (int j = 0; j < nk; ++j) {
-#pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)
-                      tc_mma(dacc, da + (uint64_t)(j * (A_BYTES >> 4)) + 2 * kk,
-                             db + (uint64_t)(j * (B_BYTES >> 4)) + 2 * kk, IDESC_N256, (accum | j | kk) ? 1u : 0u);
-                  }
-                  tc_commit(empty0 + 8 * st);
-                }
-                __syncwarp();
-                accum = 1;
+        for (int kc0 = 0; kc0 < ti.nkb && ok; kc0 += CKB, ++cc) {
+          const int kc1 = min(ti.nkb, kc0 + CKB);
+          const int buf = cc % NACC;
+          const uint32_t use = cc / NACC;
+          if (!warp_wait<true>(acce0 + 8 * buf, (use & 1) ^ 1, tmo)) {
+            if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dacc = tbase + buf * 256;
+          uint32_t accum = 0;
+          for (int kb = kc0; kb < kc1 && ok; kb += KPS) {
+            const int nk = min(KPS, kc1 - kb);
+            for (int h = 0; h < 2; ++h, ++it) {
+              const int st = it % NST;
+              if (!warp_wait(full0 + 8 * st, (it / NST) & 1, tmo)) {
+                if (lane == 0) atomicOr(P.status, ERR_TIMEOUT_MMA);
+                ok = false;
+                break;
               }
-            }
-            if (ok) {
-              if (elect_one()) tc_commit(accf0 + 8 * buf);
+              tc_fence_after();
+              const uint64_t da = descA0 + (uint64_t)(st * (STAGE_BYTES >> 4));
+              const uint64_t db = descB0 + (uint64_t)(st * (STAGE_BYTES >> 4));
+              if (elect_one()) {
+                for (int j = 0; j < nk; ++j) {
+#pragma unroll
+                  for (int kk = 0; kk < BK / 16; ++kk)
+                    tc_mma(dacc, da + (uint64_t)(j * (A_BYTES >> 4)) + 2 * kk,
+                           db + (uint64_t)(j * (B_BYTES >> 4)) + 2 * kk, IDESC_N256, (accum | j | kk) ? 1u : 0u);
+                }
+                tc_commit(empty0 + 8 * st);
+              }
               __syncwarp();
+              accum = 1;
             }
           }
+          if (ok) {
+            if (elect_one()) tc_commit(accf0 + 8 * buf);
+            __syncwarp();
+          }
+        }
       }
       if (elect_one()) tc_commit(tdown);
       __syncwarp();
@@ -942,8 +974,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
     uint32_t cc = 0;
     bool ok = true;
-    for (long long t = pair; t < P.ntiles && ok; t += npairs) {
-      long long slot;
+    for (long long un = 0; un < nunits && ok; ++un) {
+      int i;
+      long long t, slot;
+      crt_unit(un, NM, my_tiles, pair, npairs, P.crt_order, i, t);
       const Tile ti = decode_tile_crt(P, t, slot);
       const GemmProblem &pr = problem(P, ti.prob);
       const int nkc = (ti.nkb + CKB - 1) / CKB;
@@ -951,13 +985,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       auto res_ptr = [&](int i) {
         return (uint4 *)(pr.res + ((((size_t)slot * NM + i) * 2 + rank) * 256 + threadIdx.x) * 128);
       };
-      for (int i = 0; i < NM && ok; ++i) {
+      {
         int acc[128];
 #pragma unroll
         for (int u = 0; u < 128; ++u) acc[u] = 0;
         for (int kc = 0; kc < nkc && ok; ++kc, ++cc) {
           const int buf = cc % NACC;
           const uint32_t use = cc / NACC;
+          // the residues this unit adds to: one 128-byte line per thread, 4 KB
+          // per warp, brought into L2 one chunk ahead of their read
+          if (!pr.seg_first && kc == max(0, nkc - 2) && lane == 0) prefetch_l2(res_ptr(i), 32 * 128);
           int got = 0;
           if (lane == 0) got = mbar_wait(accf0 + 8 * buf, use & 1, tmo) ? 1 : 0;
           got = __shfl_sync(0xffffffffu, got, 0);
@@ -1009,7 +1046,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         }
       }
       if (!ok) break;
-      if (!pr.seg_last) continue;
+      if (!pr.seg_last || i != NM - 1) continue;
       // ---- last segment: C' from its residues (CRT), scaled to FP64 by 2^(eA + eB - 2b)
       const int row = ti.m0 + (int)rank * BM + qd * 32 + lane;
       if (row >= pr.M) continue;
@@ -1969,6 +2006,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       P.ntiles = P.nprob * cnt;
       if (crt) {
         P.crt = cc;
+        P.crt_order = ctx->crt_order;
         if (!crt_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, nkb_all, accumulate, uplo, cw.Wr, cw.Xr,
                           cw.Yr, cw.expW, cw.expX, cw.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, t0,
                           slots, cw.store, pl.nmod, pl.bits))
@@ -2363,6 +2401,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           P.timeout_ns = (unsigned long long)ctx->opt.wait_timeout_ns;
           if (crt) {
             P.crt = cc;
+            P.crt_order = ctx->crt_order;
             HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s));
           } else {
             HSG_LAUNCH(ctx, launch_gemm(P, s));

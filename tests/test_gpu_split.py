@@ -164,29 +164,34 @@ def test_moduli_error_follows_the_bits(hs):
     assert errs[3][1] < errs[2][1], errs  # 47 bits: the floor of X = T W
 
 
-def test_moduli_stage_geometries_agree_bitwise(hs, monkeypatch):
+def test_moduli_stage_geometries_and_unit_orders_agree_bitwise(hs, monkeypatch):
     """The moduli kernel's two stage geometries (3 stages of 2 k-blocks with
-    chunks of 8, 2 stages of 3 with chunks of 6) sum the same exact integers,
-    so H and S agree bit for bit."""
+    chunks of 8, 2 stages of 3 with chunks of 6) and its two orders of
+    (tile, modulus) units sum the same exact integers, so H and S agree bit
+    for bit."""
     w = make_config(1)
     out = []
-    for geom in ("0", "1"):
+    for geom, order in (("0", "0"), ("1", "0"), ("0", "1"), ("1", "1")):
         monkeypatch.setenv("HSGEN_CRT_GEOMETRY", geom)
+        monkeypatch.setenv("HSGEN_CRT_ORDER", order)
         H, S, st = run_gpu(hs, w.system, w.kvecs[0], scheme=hs.SCHEME_MODULI)
-        assert st["stage_geometry"] == int(geom)
+        assert st["stage_geometry"] == int(geom) and st["unit_order"] == int(order)
         out.append((H, S))
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
-    check(w.system, w.kvecs[0], *out[1])
+    for H, S in out[1:]:
+        assert np.array_equal(out[0][0], H) and np.array_equal(out[0][1], S)
+    check(w.system, w.kvecs[0], *out[-1])
 
 
-def test_moduli_across_many_depth_segments(hs, monkeypatch):
+@pytest.mark.parametrize("order", ["0", "1"])
+def test_moduli_across_many_depth_segments(hs, monkeypatch, order):
     """One depth segment of 64 rows per launch (41 launches at 16 atoms /
     N_G 3000): the residues of every segment add up modulo each m_i in the
     residue store, and only the last launch writes H and S."""
     monkeypatch.setenv("HSGEN_KSEG_BLOCKS", "1")
+    monkeypatch.setenv("HSGEN_CRT_ORDER", order)
     w = make_config(1)
     H, S, st = run_gpu(hs, w.system, w.kvecs[0], scheme=hs.SCHEME_MODULI)
-    assert st["kseg_blocks"] == 1 and st["scheme"] == hs.SCHEME_MODULI
+    assert st["kseg_blocks"] == 1 and st["scheme"] == hs.SCHEME_MODULI and st["unit_order"] == int(order)
     check(w.system, w.kvecs[0], H, S)
 
 
@@ -332,6 +337,7 @@ def test_split_autotune_choice_and_parity(hs):
         torch.cuda.synchronize()
         st = g.stats()
         assert st["kseg_blocks"] in (16, 24, 32, 48, 64, 96, 128, 192, 256) and st["tile_band"] in (8, 16, 32)
+        assert st["unit_order"] in (0, 1)
         H2, S2 = g.build(kd)
         torch.cuda.synchronize()
         assert torch.equal(H, H2) and torch.equal(S, S2)
