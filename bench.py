@@ -810,8 +810,8 @@ def main():
                    "target_rel_err": args.target if precision == hsgen.SPLIT else None,
                    "atom_chunks": st["atom_chunks"],
                    "schedule": ({"kseg_blocks": tuned["kseg_blocks"], "tile_band": tuned["tile_band"],
-                                 "stage_geometry": tuned["stage_geometry"],
-                                 "autotuned": not args.no_autotune,
+                                 "stage_geometry": tuned["stage_geometry"], "unit_order": tuned["unit_order"],
+                                 "l2_hint": tuned["l2_hint"], "autotuned": not args.no_autotune,
                                  "autotune_measured_rel_err": tuned["tuned_rel_err"]}
                                 if precision == hsgen.SPLIT else None),
                    "l2": "working set >> L2 (no flush needed)",

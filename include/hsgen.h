@@ -38,16 +38,19 @@
  * calls on one context are ordered (they share device workspaces): issue
  * them on one stream, or synchronise between streams.
  * Buffers on another GPU than the context's are rejected (HSGEN_EINVAL).
- * Environment (tuning only; results move at the rounding level at most):
- * HSGEN_KSEG_BLOCKS, the split form's depth segment in 64-deep blocks, and
- * HSGEN_CRT_GEOMETRY (0 or 1), the moduli kernel's stage geometry, and
- * HSGEN_CRT_ORDER (0 or 1), the order of its work units, and
- * HSGEN_TILE_BAND, the split form's tile band in 64-column blocks (all read
- * by hsgen_create; hsgen_autotune picks them per shape); HSGEN_WS_BYTES, the
- * split form's workspace budget that sets the passes over the atoms when
- * opt.atom_chunk is 0 (default 176e9); HSGEN_BATCH_BYTES,
- * the operand-memory budget of one batched group; HSGEN_REDUCE_BLOCK, the
- * block rows of hsgen_reduce_generalized (default 128).
+ * Environment (tuning only; results move at the rounding level at most;
+ * read by hsgen_create, and hsgen_autotune picks the first five per shape):
+ *  HSGEN_KSEG_BLOCKS   the split form's depth segment, in 64-deep blocks;
+ *  HSGEN_TILE_BAND     the split form's tile band, in 64-column blocks;
+ *  HSGEN_CRT_ORDER     0 or 1, the order of the moduli kernel's work units;
+ *  HSGEN_L2_HINT       0 or 8, the L2 priority of its operand loads;
+ *  HSGEN_CRT_GEOMETRY  0 or 1, its pipeline stage geometry;
+ *  HSGEN_WS_BYTES      the split form's workspace budget, which sets the
+ *                      passes over the atoms when opt.atom_chunk is 0
+ *                      (default 176e9);
+ *  HSGEN_BATCH_BYTES   the operand-memory budget of one batched group;
+ *  HSGEN_REDUCE_BLOCK  the block rows of hsgen_reduce_generalized
+ *                      (default 128).
  * Fault injection (tests): HSGEN_FAIL_ALLOC=1 makes every growth of a
  * library workspace fail as an out-of-memory cudaMalloc would (the call
  * returns HSGEN_ENOMEM; the context stays usable once the variable is unset).
@@ -168,6 +171,9 @@ typedef struct {
                            /* units, 0: every modulus of a tile before the next */
                            /* tile, 1: every tile of a modulus before the next  */
                            /* modulus                                           */
+  int l2_hint;             /* moduli scheme: L2 priority of its operand loads,  */
+                           /* 0: normal, 8: the column operand (re-read by the  */
+                           /* next waves of a band) evict-last                  */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -283,8 +289,9 @@ hsgen_status hsgen_depth_layout(hsgen_ctx *ctx, int *offsets, int capacity);
  * depth-segment lengths {64, 96, 128, 192, 256} blocks of 64 (moduli scheme:
  * {64, 128, 256} in modulus-major unit order and 32 in tile-major order;
  * tile band 16), then tile bands {8, 32} with the best segment, then, for
- * the moduli scheme, its kernel's other stage geometry
- * (hsgen_stats unit_order, stage_geometry). The choices stay in the
+ * the moduli scheme, the other L2 priority of its operand loads and its
+ * kernel's other stage geometry (hsgen_stats unit_order, l2_hint,
+ * stage_geometry). The choices stay in the
  * context for later builds (batched ones use the schedule) and H and S are
  * left built with them. Same arguments as hsgen_build_HS; synchronous; about
  * ten to fifteen builds long. The FP64 form has nothing to tune: it builds

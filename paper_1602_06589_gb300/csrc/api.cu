@@ -213,6 +213,7 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   if (const char *cg = std::getenv("HSGEN_CRT_GEOMETRY")) ctx->crt_geom = std::atoi(cg) == 1 ? 1 : 0;
   if (const char *co = std::getenv("HSGEN_CRT_ORDER")) ctx->crt_order = std::atoi(co) == 1 ? 1 : 0;
   if (const char *tb = std::getenv("HSGEN_TILE_BAND")) ctx->tile_band = std::max(1, std::atoi(tb));
+  if (const char *lh = std::getenv("HSGEN_L2_HINT")) ctx->l2_hint = std::atoi(lh) & 15;
   if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess ||
       split_upload_tables() != cudaSuccess) {
     delete ctx;
@@ -1028,8 +1029,18 @@ hsgen_status hsgen_autotune(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
       best_b = band;
     }
   }
-  // moduli scheme: the stage geometry of its kernel (3 stages of 2 k-blocks
-  // or 2 stages of 3)
+  // moduli scheme: the L2 priority of its operand loads (B evict-last or
+  // both normal), then the stage geometry of its kernel (3 stages of 2
+  // k-blocks or 2 stages of 3)
+  if (ctx->last_plan.scheme == kSchemeModuli) {
+    const int h0 = ctx->l2_hint;
+    ctx->l2_hint = h0 ? 0 : 8;
+    double ms = 0.0;
+    hsgen_status st = trial(best_k, best_b, ms);
+    if (st != HSGEN_OK) return st;
+    if (ms < best) best = ms;
+    else ctx->l2_hint = h0;
+  }
   if (ctx->last_plan.scheme == kSchemeModuli) {
     const int g0 = ctx->crt_geom;
     int best_g = g0;
@@ -1084,6 +1095,7 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   st.tile_band = ctx->tile_band;
   st.stage_geometry = ctx->crt_geom;
   st.unit_order = ctx->crt_order;
+  st.l2_hint = ctx->l2_hint;
   *out = st;
   // the stats are filled in either way; a wait that expired is reported here
   return split_poll_status(ctx, true);

@@ -124,6 +124,7 @@ struct hsgen_ctx {
   int auto_chunk = 0;               // atoms per pass chosen by the library (0: all), see atom_chunk
   int crt_geom = 0;                 // moduli kernel's stage geometry (0: 3 x 2 k-blocks, 1: 2 x 3)
   int crt_order = 1;                // moduli kernel's unit order (0: tile-major, 1: modulus-major)
+  int l2_hint = 8;                  // moduli kernel's L2 priorities of its A and B loads (8: B evict-last)
   std::vector<int2> tiles_host;     // host copy of that list (column bands of the overlapped copies)
   cudaStream_t copy_stream = nullptr;  // host outputs: copies of finished column bands
   cudaEvent_t copy_ev = nullptr;       // orders each copy after the launch that finished its bands

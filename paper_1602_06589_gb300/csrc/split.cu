@@ -145,6 +145,7 @@ struct GemmParams {
   unsigned long long timeout_ns;
   CrtConsts crt;  // moduli form only
   int crt_order;  // moduli form: 0 tile-major units, 1 modulus-major (see crt_unit)
+  int l2_hint;    // moduli form: L2 priority of A (bits 0-1) and B (bits 2-3) loads: 0 normal, 1 first, 2 last
 };
 
 // ---------------------------------------------------------------------------
@@ -191,6 +192,30 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       " [%0], [%1, {%3, %4, %5}], [%2];"
       ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
+}
+// The same load with an L2 eviction-priority hint (a policy from createpolicy).
+__device__ __forceinline__ void tma_load_3d_hint(uint32_t dst, const CUtensorMap *map, uint32_t mbar, int c0, int c1,
+                                                 int c2, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4, %5}], [%2], %6;"
+      ::"r"(dst), "l"((uint64_t)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 __device__ __forceinline__ uint32_t cta_rank() {
   uint32_t r;
@@ -863,6 +888,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // ------------------------------ TMA producer ------------------------------
     uint32_t it = 0;
     bool ok = true;
+    auto policy = [](int h) {
+      return h == 1 ? policy_evict_first() : h == 2 ? policy_evict_last() : policy_evict_normal();
+    };
+    const uint64_t polA = policy(P.l2_hint & 3), polB = policy((P.l2_hint >> 2) & 3);
     for (long long un = 0; un < nunits && ok; ++un) {
       int i;
       long long t, slot;
@@ -890,8 +919,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           if (elect_one()) {
             if (leader) mbar_expect_tx(full0 + 8 * st, bytes);
             for (int j = 0; j < nk; ++j) {
-              tma_load_3d(sA0 + j * A_BYTES, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA + j);
-              tma_load_3d(sA0 + STAGE_A + j * B_BYTES, mB, mbar, 0, ti.n0, pb * pr.b_nkb + kbA + j);
+              tma_load_3d_hint(sA0 + j * A_BYTES, mA, mbar, 0, ti.m0 + (int)rank * BM, pa * pr.a_nkb + kbA + j, polA);
+              tma_load_3d_hint(sA0 + STAGE_A + j * B_BYTES, mB, mbar, 0, ti.n0, pb * pr.b_nkb + kbA + j, polB);
             }
           }
           __syncwarp();
@@ -2007,6 +2036,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
       if (crt) {
         P.crt = cc;
         P.crt_order = ctx->crt_order;
+        P.l2_hint = ctx->l2_hint;
         if (!crt_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, nkb_all, accumulate, uplo, cw.Wr, cw.Xr,
                           cw.Yr, cw.expW, cw.expX, cw.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, t0,
                           slots, cw.store, pl.nmod, pl.bits))
@@ -2402,6 +2432,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           if (crt) {
             P.crt = cc;
             P.crt_order = ctx->crt_order;
+            P.l2_hint = ctx->l2_hint;
             HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s));
           } else {
             HSG_LAUNCH(ctx, launch_gemm(P, s));

@@ -51,7 +51,8 @@ class Stats(C.Structure):
                 ("ms_s", C.c_double), ("kseg_blocks", C.c_int), ("tile_band", C.c_int),
                 ("ms_upload", C.c_double), ("ms_download", C.c_double), ("scheme", C.c_int), ("moduli", C.c_int),
                 ("bits", C.c_int), ("products", C.c_int), ("atom_chunks", C.c_int), ("tuned_rel_err", C.c_double),
-                ("stage_geometry", C.c_int), ("unit_order", C.c_int)]
+                ("stage_geometry", C.c_int), ("unit_order", C.c_int),
+                ("l2_hint", C.c_int)]
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_blocks",

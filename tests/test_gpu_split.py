@@ -166,16 +166,17 @@ def test_moduli_error_follows_the_bits(hs):
 
 def test_moduli_stage_geometries_and_unit_orders_agree_bitwise(hs, monkeypatch):
     """The moduli kernel's two stage geometries (3 stages of 2 k-blocks with
-    chunks of 8, 2 stages of 3 with chunks of 6) and its two orders of
-    (tile, modulus) units sum the same exact integers, so H and S agree bit
-    for bit."""
+    chunks of 8, 2 stages of 3 with chunks of 6), its two orders of
+    (tile, modulus) units and its L2 priorities sum the same exact integers,
+    so H and S agree bit for bit."""
     w = make_config(1)
     out = []
-    for geom, order in (("0", "0"), ("1", "0"), ("0", "1"), ("1", "1")):
+    for geom, order, hint in (("0", "0", "0"), ("1", "0", "8"), ("0", "1", "0"), ("1", "1", "8")):
         monkeypatch.setenv("HSGEN_CRT_GEOMETRY", geom)
         monkeypatch.setenv("HSGEN_CRT_ORDER", order)
+        monkeypatch.setenv("HSGEN_L2_HINT", hint)
         H, S, st = run_gpu(hs, w.system, w.kvecs[0], scheme=hs.SCHEME_MODULI)
-        assert st["stage_geometry"] == int(geom) and st["unit_order"] == int(order)
+        assert st["stage_geometry"] == int(geom) and st["unit_order"] == int(order) and st["l2_hint"] == int(hint)
         out.append((H, S))
     for H, S in out[1:]:
         assert np.array_equal(out[0][0], H) and np.array_equal(out[0][1], S)
