@@ -87,6 +87,17 @@ enum { HSGEN_S_CONTRACTION = 0, HSGEN_S_LEGENDRE = 1 };
  *  HSGEN_SCHEME_AUTO: moduli when a count of at most 14 meets target_rel_err
  *    (and no slice count is forced), otherwise slices. */
 enum { HSGEN_SCHEME_AUTO = 0, HSGEN_SCHEME_SLICES = 1, HSGEN_SCHEME_MODULI = 2 };
+/* How an atom's contribution to H is formed (Sec. 4.6.2-4.6.3, Listings
+ * alg:H_AA_HPD and alg:H_AA_dynamic):
+ *  HSGEN_H_TW: X_a = T W_a and H += W_a^H X_a for every atom;
+ *  HSGEN_H_HPD: hsgen_set_atoms factors each species' T (the rows the
+ *    contraction uses) as T = C C^H; a species whose factorization succeeds
+ *    (LAPACK potrf status 0, hsgen_T_factor) takes Y_a = C^H W_a and
+ *    H += Y_a^H Y_a, the others X = T W as above. The paper tests T^[AA] only,
+ *    because its H_AA is a separate product; here T's four blocks stay one
+ *    matrix, so the test covers all of it. Passes over the atoms are split
+ *    where the route changes (order atoms by species to keep them few). */
+enum { HSGEN_H_TW = 0, HSGEN_H_HPD = 1 };
 
 typedef struct {
   int precision;            /* HSGEN_FP64 (default) or HSGEN_SPLIT                  */
@@ -105,6 +116,7 @@ typedef struct {
   int scheme;               /* split form: HSGEN_SCHEME_* (default AUTO)            */
   int moduli;               /* split form, moduli scheme: 10..14, 0 = from the      */
                             /* target and the depth                                 */
+  int h_form;               /* HSGEN_H_TW (default) or HSGEN_H_HPD                  */
 } hsgen_options;
 
 /* Radial data of one atom species (App. A.1 and A.2). All arrays are host
@@ -174,6 +186,7 @@ typedef struct {
   int l2_hint;             /* moduli scheme: L2 priority of its operand loads,  */
                            /* 0: normal, 8: the column operand (re-read by the  */
                            /* next waves of a band) evict-last                  */
+  int hpd_species;         /* species on the HPD route (opt.h_form HSGEN_H_HPD) */
 } hsgen_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -273,6 +286,15 @@ hsgen_status hsgen_coefficients_noalloc(hsgen_ctx *ctx, int n_g, const double *k
 /* T of species `type` (a2) copied into T (host, (2N_L)^2 complex, column-major),
  * with the l_nonsph structure of Fig. Tmat_structure. */
 hsgen_status hsgen_T_matrix(hsgen_ctx *ctx, int type, double *T);
+/* Cholesky factor of species `type`'s T (Sec. 4.6.2-4.6.3; set by
+ * hsgen_set_atoms when opt.h_form is HSGEN_H_HPD, HSGEN_EINVAL otherwise):
+ * *info receives the status of the factorization (0: T is Hermitian positive
+ * definite; k > 0: the leading minor of order k is not, as LAPACK potrf
+ * reports it) and C (host, (2N_L')^2 complex, column-major, or NULL) the
+ * lower factor C with T = C C^H (for k > 0, its first k - 1 columns, zeros
+ * elsewhere). N_L' = N_L, or (l_nonsph + 1)^2 with S in the Legendre form
+ * (the rows the contraction uses). */
+hsgen_status hsgen_T_factor(hsgen_ctx *ctx, int type, double *C, int *info);
 /* Row offsets of the atoms in the depth of W (offsets[n_atoms+1], host); the
  * block of atom a is offsets[a] .. offsets[a] + 2 N_La (A rows, then B rows),
  * followed by zero rows up to offsets[a+1]. */

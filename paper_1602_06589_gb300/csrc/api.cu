@@ -135,6 +135,7 @@ static void free_system(hsgen_ctx *ctx) {
     if (sp.d_T) cudaFree(sp.d_T);
     if (sp.d_Tsl) cudaFree(sp.d_Tsl);
     if (sp.d_Texp) cudaFree(sp.d_Texp);
+    if (sp.d_C) cudaFree(sp.d_C);
   }
   ctx->types.clear();
   ctx->split_slices = 0;
@@ -152,11 +153,21 @@ static void free_system(hsgen_ctx *ctx) {
 }
 
 // Chunks of atoms [a0, a1) processed per pass over the depth (a6).
+// Passes over the atoms: ranges of at most the chunk size, also cut where
+// the H route changes from one atom to the next (every pass takes one route).
 static std::vector<std::pair<int, int>> atom_chunks(const hsgen_ctx *ctx) {
   int na = (int)ctx->toa.size();
   int c = ctx->opt.atom_chunk > 0 ? ctx->opt.atom_chunk : (ctx->auto_chunk > 0 ? ctx->auto_chunk : na);
   std::vector<std::pair<int, int>> out;
-  for (int a = 0; a < na; a += c) out.push_back({a, std::min(na, a + c)});
+  for (int a = 0; a < na; a += c) {
+    const int e = std::min(na, a + c);
+    int b = a;
+    for (int k = a + 1; k <= e; ++k)
+      if (k == e || ctx->types[ctx->toa[k]].routed != ctx->types[ctx->toa[b]].routed) {
+        out.push_back({b, k});
+        b = k;
+      }
+  }
   return out;
 }
 
@@ -179,6 +190,7 @@ hsgen_status hsgen_default_options(hsgen_options *opt) {
   opt->s_form = HSGEN_S_CONTRACTION;
   opt->scheme = HSGEN_SCHEME_AUTO;
   opt->moduli = 0;
+  opt->h_form = HSGEN_H_TW;
   return HSGEN_OK;
 }
 
@@ -196,6 +208,7 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   if (o.scheme != HSGEN_SCHEME_AUTO && o.scheme != HSGEN_SCHEME_SLICES && o.scheme != HSGEN_SCHEME_MODULI)
     return HSGEN_EINVAL;
   if (o.moduli != 0 && (o.moduli < kMinModuli || o.moduli > 14)) return HSGEN_EINVAL;
+  if (o.h_form != HSGEN_H_TW && o.h_form != HSGEN_H_HPD) return HSGEN_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -386,11 +399,43 @@ hsgen_status hsgen_set_atoms(hsgen_ctx *ctx, const double *lattice, double omega
     }
   }
   HSG_CUDA(ctx, cudaFree(d_scratch));
+  // HPD route: the Cholesky test of every species' T (Sec. 4.6.3)
+  if (ctx->opt.h_form == HSGEN_H_HPD) {
+    int *d_info = nullptr;
+    HSG_CUDA(ctx, cudaMalloc(&d_info, sizeof(int)));
+    for (auto &sp : ctx->types) {
+      cudaError_t e = cudaMalloc(&sp.d_C, sizeof(double2) * (size_t)sp.dpad * sp.dpad);
+      if (e == cudaSuccess) e = launch_cholesky(sp, (const double2 *)sp.d_T, (double2 *)sp.d_C, d_info, 0);
+      if (e == cudaSuccess) e = cudaMemcpy(&sp.hpd_info, d_info, sizeof(int), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        cudaFree(d_info);
+        return cuda_err(ctx, e, "Cholesky test of T");
+      }
+      sp.routed = sp.hpd_info == 0;
+    }
+    HSG_CUDA(ctx, cudaFree(d_info));
+  }
   if (ctx->opt.precision == HSGEN_SPLIT) {
     hsgen_status st = split_prepare_types(ctx, choose_slices(ctx->opt.target_rel_err, ctx->opt.slices));
     if (st != HSGEN_OK) return st;
   }
   ctx->have_system = true;
+  return HSGEN_OK;
+}
+
+hsgen_status hsgen_T_factor(hsgen_ctx *ctx, int type, double *C, int *info) {
+  if (!ctx || !info) return HSGEN_EINVAL;
+  if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "T_factor: no system set");
+  if (type < 0 || type >= (int)ctx->types.size()) return set_err(ctx, HSGEN_EINVAL, "T_factor: bad type");
+  const Species &sp = ctx->types[type];
+  if (!sp.d_C) return set_err(ctx, HSGEN_EINVAL, "T_factor: T is factored only with opt.h_form HSGEN_H_HPD");
+  *info = sp.hpd_info;
+  if (C) {
+    const int n = 2 * sp.nlc;
+    HSG_CUDA(ctx, cudaSetDevice(ctx->device));
+    HSG_CUDA(ctx, cudaMemcpy2D(C, sizeof(double2) * n, sp.d_C, sizeof(double2) * sp.dpad, sizeof(double2) * n, n,
+                               cudaMemcpyDeviceToHost));
+  }
   return HSGEN_OK;
 }
 
@@ -538,14 +583,16 @@ static hsgen_status run_kpoint(hsgen_ctx *ctx, const KpointJob &job, cudaStream_
         while (hi < (int)lst.size() && lst[hi] < a1) ++hi;
         if (hi == lo) continue;
         const int *d_atoms = ctx->d_atoms_by_type + ctx->atoms_by_type_start[t] + lo;
-        HSG_LAUNCH(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].d_T, d_atoms,
-                                           hi - lo, ctx->d_off, row_base, W, X, L.ldw, s));
+        HSG_LAUNCH(ctx, launch_tapply_fp64(ctx->types[t].dpad, n_g, (const double2 *)ctx->types[t].apply_matrix(),
+                                           d_atoms, hi - lo, ctx->d_off, row_base, W, X, L.ldw, s));
       }
       if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 2), s));
       if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 3), s));
+      // a pass on the HPD route holds Y = C^H W in X: H += Y^H Y
+      const bool gram = ctx->types[ctx->toa[a0]].routed;
       HSG_LAUNCH(ctx, launch_hs_fp64(n_g, cdepth, W, X, ctx->d_urow + row_base, L.ldw, job.H,
                                      job.leg ? nullptr : job.S, job.ld, ctx->opt.uplo, ci > 0 ? 1 : 0, ctx->owner,
-                                     s));
+                                     s, gram));
     }
     if (record) HSG_CUDA(ctx, cudaEventRecord(cev(ci, 4), s));
   }
@@ -1096,6 +1143,8 @@ hsgen_status hsgen_get_stats(hsgen_ctx *ctx, hsgen_stats *out) {
   st.stage_geometry = ctx->crt_geom;
   st.unit_order = ctx->crt_order;
   st.l2_hint = ctx->l2_hint;
+  st.hpd_species = 0;
+  for (const auto &sp : ctx->types) st.hpd_species += sp.routed ? 1 : 0;
   *out = st;
   // the stats are filled in either way; a wait that expired is reported here
   return split_poll_status(ctx, true);

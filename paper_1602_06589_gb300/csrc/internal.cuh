@@ -40,6 +40,15 @@ struct Species {
   int *d_Texp = nullptr;
   int t_kspan = 0;
   int t_real = 0;                  // imaginary part of T identically zero
+  // HPD route (option h_form HSGEN_H_HPD, Sec. 4.6.2-4.6.3): the Cholesky
+  // factor C of the contraction block of T (T = C C^H, lower, dpad x dpad) and
+  // the status of its factorization (0: HPD); a routed species multiplies its
+  // atoms' W by C^H instead of T, and its H contribution is (C^H W)^H (C^H W).
+  double *d_C = nullptr;
+  int hpd_info = -1;
+  bool routed = false;
+  // the matrix P of the T-apply step X = P^H W (T is Hermitian: P = T)
+  const double *apply_matrix() const { return routed ? d_C : d_T; }
 };
 
 // Per-species radial parameters read by the radial-factor kernel.
@@ -208,16 +217,19 @@ hsgen_status legendre_S(hsgen_ctx *ctx, int n_g, const double *kvec_dev, const d
                         void *ws, double2 *S, double2 *H, long long ld, cudaStream_t s, void *S_host = nullptr);
 // a2: T matrix of one species (device, dpad x dpad complex, column-major).
 cudaError_t launch_tmatrix(const Species &sp, double2 *d_T, double *scratch, cudaStream_t s);
+// Cholesky factor of the species' T into d_C and its status into *d_info (device).
+cudaError_t launch_cholesky(const Species &sp, const double2 *d_T, double2 *d_C, int *d_info, cudaStream_t s);
 // Recurrence tables in constant memory (called once per device).
 cudaError_t upload_tables();
 // a3: X_a = T_type W_a for all atoms of one species (FP64 DMMA).
 cudaError_t launch_tapply_fp64(int dpad, int n_g, const double2 *T, const int *atoms, int n_atoms,
                                const int *off, int row_base, const double2 *W, double2 *X, long long ldw,
                                cudaStream_t s);
-// a4: upper (or lower) triangle of H += W^H X and S += W^H diag(u) W (FP64 DMMA).
+// a4: upper (or lower) triangle of H += W^H X and S += W^H diag(u) W (FP64 DMMA);
+// gram (the HPD route, X = C^H W): H += X^H X instead.
 cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *X, const double *urow,
                            long long ldw, double2 *H, double2 *S, long long ld, int uplo, int accumulate,
-                           const BlockOwner &own, cudaStream_t s);
+                           const BlockOwner &own, cudaStream_t s, bool gram = false);
 // C (+)= (+-) P^H Q in FP64 (DMMA): P is K x M, Q is K x N (complex, column-major), C is M x N;
 // uplo 'U': only the entries i <= j (diagonal imaginary parts set to 0); C must not overlap P or Q.
 cudaError_t launch_gemm_fp64(int M, int N, int K, const double2 *P, long long ldp, const double2 *Q, long long ldq,

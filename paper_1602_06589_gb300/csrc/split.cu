@@ -1626,7 +1626,14 @@ hsgen_status tapply_split(hsgen_ctx *ctx, int n_g, int a0, int a1, const __nv_bf
 bool hs_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, long long ldk, int kb0, int seg,
                  bool accumulate, int uplo, const __nv_bfloat16 *Wsl, const __nv_bfloat16 *Xsl,
                  const __nv_bfloat16 *Ysl, const int *expW, const int *expX, const int *expY, double2 *H, double2 *S,
-                 long long ld, const int2 *tiles, long long ntiles, long long tile_begin, int slices) {
+                 long long ld, const int2 *tiles, long long ntiles, long long tile_begin, int slices, bool gram) {
+  // gram (HPD route, X = C^H W): H = X^H X, X's planes on both sides; S unchanged
+  const __nv_bfloat16 *Wsl0 = Wsl;
+  const int *expW0 = expW;
+  if (gram) {
+    Wsl = Xsl;
+    expW = expX;
+  }
   for (int k = 0; k < (S ? 2 : 1); ++k) {
     GemmProblem &q = pr[k];
     std::memset(&q, 0, sizeof(q));
@@ -1641,7 +1648,7 @@ bool hs_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, lon
     q.accumulate = (accumulate || kb0 > 0) ? 1 : 0;
     q.F = fixed_point_bits(seg * BK);
     q.expA = (k == 0) ? expW : expY;
-    q.expB = (k == 0) ? expX : expW;
+    q.expB = (k == 0) ? expX : expW0;
     q.C = (k == 0) ? H : S;
     q.ldc = ld;
     q.n_batch = 1;
@@ -1651,7 +1658,7 @@ bool hs_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, lon
     q.tile_begin = tile_begin + k * ntiles;
     q.a_nkb = q.b_nkb = (int)(ldk / BK);
     const void *a = (k == 0) ? (const void *)Wsl : (const void *)Ysl;
-    const void *b = (k == 0) ? (const void *)Xsl : (const void *)Wsl;
+    const void *b = (k == 0) ? (const void *)Xsl : (const void *)Wsl0;
     if (!make_map(&mA[k], a, q.a_nkb, n_g, (long long)q.a_pps * slices, BM) ||
         !make_map(&mB[k], b, q.b_nkb, n_g, 3LL * slices, BN))
       return false;
@@ -1666,7 +1673,7 @@ bool crt_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, lo
                   int nkb_all, bool accumulate, int uplo, const __nv_bfloat16 *Wr, const __nv_bfloat16 *Xr,
                   const __nv_bfloat16 *Yr, const int *expW, const int *expX, const int *expY, double2 *H, double2 *S,
                   long long ld, const int2 *tiles, long long ntiles, long long tile_begin, long long slot0,
-                  long long slots_per_matrix, unsigned char *store, int nmod, int bits) {
+                  long long slots_per_matrix, unsigned char *store, int nmod, int bits, bool gram) {
   for (int k = 0; k < (S ? 2 : 1); ++k) {
     GemmProblem &q = pr[k];
     std::memset(&q, 0, sizeof(q));
@@ -1679,7 +1686,8 @@ bool crt_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, lo
     q.uplo = uplo;
     q.accumulate = accumulate ? 1 : 0;
     q.F = 2 * bits;
-    q.expA = (k == 0) ? expW : expY;
+    // gram (HPD route, X = C^H W): H = X^H X, X's residues on both sides
+    q.expA = (k == 0) ? (gram ? expX : expW) : expY;
     q.expB = (k == 0) ? expX : expW;
     q.C = (k == 0) ? H : S;
     q.ldc = ld;
@@ -1693,7 +1701,7 @@ bool crt_problems(GemmProblem *pr, CUtensorMap *mA, CUtensorMap *mB, int n_g, lo
     q.res_base = k * slots_per_matrix + slot0;
     q.seg_first = kb0 == 0;
     q.seg_last = kb0 + seg >= nkb_all;
-    const void *a = (k == 0) ? (const void *)Wr : (const void *)Yr;
+    const void *a = (k == 0) ? (gram ? (const void *)Xr : (const void *)Wr) : (const void *)Yr;
     const void *b = (k == 0) ? (const void *)Xr : (const void *)Wr;
     if (!make_map(&mA[k], a, q.a_nkb, n_g, (long long)q.a_pps * nmod, BM) ||
         !make_map(&mB[k], b, q.b_nkb, n_g, 3LL * nmod, BNC))
@@ -1914,8 +1922,9 @@ hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
     double2 *Tsh = nullptr;
     HSG_CUDA(ctx, cudaMalloc(&Tsh, sizeof(double2) * span * kTShifts));
     HSG_CUDA(ctx, cudaMemset(Tsh, 0, sizeof(double2) * span * kTShifts));
+    // (the matrix P of X = P^H W: T, or its Cholesky factor C on the HPD route)
     for (int d = 0; d < kTShifts; ++d)
-      HSG_CUDA(ctx, cudaMemcpy2D(Tsh + d * span + kTShiftStep * d, sizeof(double2) * sp.t_kspan, sp.d_T,
+      HSG_CUDA(ctx, cudaMemcpy2D(Tsh + d * span + kTShiftStep * d, sizeof(double2) * sp.t_kspan, sp.apply_matrix(),
                                  sizeof(double2) * sp.dpad, sizeof(double2) * sp.dpad, sp.dpad,
                                  cudaMemcpyDeviceToDevice));
     HSG_CUDA(ctx, cudaMalloc(&sp.d_Tsl, span * 2 * slices * kTShifts * sizeof(__nv_bfloat16)));
@@ -1926,9 +1935,9 @@ hsgen_status split_prepare_types(hsgen_ctx *ctx, int slices) {
                                  sp.d_Texp, sp.dpad, 0));
     HSG_CUDA(ctx, cudaDeviceSynchronize());
     cudaFree(Tsh);
-    // does T have an imaginary part?
+    // does it have an imaginary part?
     std::vector<double2> h((size_t)sp.dpad * sp.dpad);
-    HSG_CUDA(ctx, cudaMemcpy(h.data(), sp.d_T, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost));
+    HSG_CUDA(ctx, cudaMemcpy(h.data(), sp.apply_matrix(), sizeof(double2) * h.size(), cudaMemcpyDeviceToHost));
     sp.t_real = 1;
     for (auto &v : h)
       if (v.y != 0.0) {
@@ -1974,11 +1983,15 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
   }
   if (phase_ev) HSG_CUDA(ctx, cudaEventRecord(phase_ev[0], s));
   // (3) the operands of the contraction: X (right operand of H), W (left of
-  // H, right of S) and U W (left of S), as residues or slices
+  // H, right of S) and U W (left of S), as residues or slices. A pass on the
+  // HPD route (Sec. 4.6.2) holds Y = C^H W in X and forms H = Y^H Y: W is then
+  // an operand of S only, and without S its residues are not needed.
+  const bool gram = ctx->types[ctx->toa[a0]].routed;
   const CrtConsts cc = crt ? make_crt(pl.nmod) : CrtConsts{};
   if (crt) {
     HSG_LAUNCH(ctx, launch_residue(X, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Xr, ldk, plane, cw.expX, n_g, s));
-    HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Wr, ldk, plane, cw.expW, n_g, s));
+    if (S || !gram)
+      HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Wr, ldk, plane, cw.expW, n_g, s));
     if (S)
       HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, ctx->d_urow + row_base, pl.bits, cc, 2, cw.Yr, ldk, plane,
                                      cw.expY, n_g, s));
@@ -2039,13 +2052,13 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
         P.l2_hint = ctx->l2_hint;
         if (!crt_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, nkb_all, accumulate, uplo, cw.Wr, cw.Xr,
                           cw.Yr, cw.expW, cw.expX, cw.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, t0,
-                          slots, cw.store, pl.nmod, pl.bits))
+                          slots, cw.store, pl.nmod, pl.bits, gram))
           return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S, moduli)");
         HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s));
         return HSGEN_OK;
       }
       if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
-                       w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, slices))
+                       w.expX, w.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, slices, gram))
         return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S)");
       HSG_LAUNCH(ctx, launch_gemm(P, s));
       return HSGEN_OK;
@@ -2161,6 +2174,10 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   if (ctx->opt.atom_chunk > 0 && ctx->opt.atom_chunk < na) return HSGEN_ENOTSUP;
   if (!ctx->have_system) return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: no system set");
   if (ctx->opt.fill_full) return HSGEN_ENOTSUP;
+  // one pass over all atoms: every species on one H route (HPD route: H = Y^H Y)
+  const bool gram = ctx->types[ctx->toa[0]].routed;
+  for (const auto &sp : ctx->types)
+    if (sp.routed != gram) return HSGEN_ENOTSUP;
   for (int k = 0; k < n_k; ++k) {
     if (n_g[k] < 0 || ld[k] < n_g[k] || (n_g[k] > 0 && (!kvec[k] || !H[k] || !S[k])))
       return set_err(ctx, HSGEN_EINVAL, "build_HS_batched: bad size, leading dimension or pointer");
@@ -2329,10 +2346,10 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
         const bool ok =
             crt ? crt_problems(pr2, ma, mb, n_g[k], ldk, kb0, seg, nkb_all, false, uplo, Wsl, Xsl, Ysl, eW, eX, eY,
                                (double2 *)H[k], leg ? nullptr : (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k,
-                               tiles, 0, kslots[k], store, pl.nmod, pl.bits)
+                               tiles, 0, kslots[k], store, pl.nmod, pl.bits, gram)
                 : hs_problems(pr2, ma, mb, n_g[k], ldk, kb0, seg, false, uplo, Wsl, Xsl, Ysl, eW, eX, eY,
                               (double2 *)H[k], leg ? nullptr : (double2 *)S[k], ld[k], d_tl + tl_off[k], nt_k, tiles,
-                              slices);
+                              slices, gram);
         if (!ok) return set_err(ctx, HSGEN_ECUDA, "batched: cuTensorMapEncodeTiled failed");
         const int np_k = leg ? 1 : 2;  // H (and S) of this k-point
         for (int j = 0; j < np_k; ++j) {
@@ -2407,7 +2424,8 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           if (st2 != HSGEN_OK) return st2;
           if (crt) {
             HSG_LAUNCH(ctx, launch_residue(X, depth, depth, nullptr, pl.bits, cc, 3, Xsl, ldk, plane, eX, ng, s));
-            HSG_LAUNCH(ctx, launch_residue(W, depth, depth, nullptr, pl.bits, cc, 3, Wsl, ldk, plane, eW, ng, s));
+            if (!leg || !gram)
+              HSG_LAUNCH(ctx, launch_residue(W, depth, depth, nullptr, pl.bits, cc, 3, Wsl, ldk, plane, eW, ng, s));
             if (!leg)
               HSG_LAUNCH(ctx, launch_residue(W, depth, depth, ctx->d_urow, pl.bits, cc, 2, Ysl, ldk, plane, eY, ng,
                                              s));

@@ -167,4 +167,66 @@ cudaError_t launch_tmatrix(const Species &sp, double2 *d_T, double *scratch, cud
   return cudaGetLastError();
 }
 
+// HPD test of a species' T (Sec. 4.6.2-4.6.3: the Cholesky factorization whose
+// status routes an atom's H contribution): the n x n leading block of C (the
+// contraction's rows of T, lower triangle read; leading dimension ld) is
+// factored in place as T = C C^H, C lower triangular with a real positive
+// diagonal, column by column (right-looking) by one CTA. *info = 0 when every
+// pivot is positive and finite; otherwise k, the order of the first leading
+// minor that is not positive definite (LAPACK potrf's status), and C keeps
+// only its first k - 1 columns. The strict upper triangle is zeroed.
+__global__ void __launch_bounds__(1024) cholesky_kernel(int n, int ld, double2 *C, int *info) {
+  __shared__ double s_piv;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = C[j + (size_t)j * ld].x;
+      if (!(d > 0.0) || !isfinite(d))
+        s_bad = j + 1;
+      else
+        s_piv = sqrt(d);
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const double c = s_piv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double2 v = C[i + (size_t)j * ld];
+      C[i + (size_t)j * ld] = make_double2(v.x / c, v.y / c);
+    }
+    if (threadIdx.x == 0) C[j + (size_t)j * ld] = make_double2(c, 0.0);
+    __syncthreads();
+    // trailing lower triangle: C_rq -= C_rj conj(C_qj), j < q <= r < n
+    const int m = n - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int q = j + 1 + e / m, r = j + 1 + e % m;
+      if (r < q) continue;
+      const double2 a = C[r + (size_t)j * ld], b = C[q + (size_t)j * ld];
+      double2 t = C[r + (size_t)q * ld];
+      t.x -= a.x * b.x + a.y * b.y;
+      t.y -= a.y * b.x - a.x * b.y;
+      C[r + (size_t)q * ld] = t;
+    }
+    __syncthreads();
+  }
+  const int bad = s_bad;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int r = e % n, q = e / n;
+    if (r < q || (bad && q >= bad - 1)) C[r + (size_t)q * ld] = make_double2(0.0, 0.0);
+  }
+  if (threadIdx.x == 0) *info = bad;
+}
+
+cudaError_t launch_cholesky(const Species &sp, const double2 *d_T, double2 *d_C, int *d_info, cudaStream_t s) {
+  const int n = 2 * sp.nlc;
+  cudaError_t e = cudaMemsetAsync(d_C, 0, sizeof(double2) * (size_t)sp.dpad * sp.dpad, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy2DAsync(d_C, sizeof(double2) * sp.dpad, d_T, sizeof(double2) * sp.dpad, sizeof(double2) * n, n,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  cholesky_kernel<<<1, 1024, 0, s>>>(n, sp.dpad, d_C, d_info);
+  return cudaGetLastError();
+}
+
 }  // namespace hsg

@@ -49,9 +49,10 @@ __device__ __forceinline__ void load_tile(double2 *sm, const double2 *__restrict
   }
 }
 
-// One CTA computes a 64 x 64 complex tile of C1 = P^H Q (and, if DUAL,
-// C2 = P^H diag(u) P restricted to the same rows/columns).
-template <bool DUAL>
+// One CTA computes a 64 x 64 complex tile of C1 = P^H Q, or with UQ of
+// C1 = P^H diag(u) Q (and, if DUAL, C2 = P^H diag(u) P restricted to the same
+// rows/columns).
+template <bool DUAL, bool UQ = false>
 __device__ __forceinline__ void tile_mma(const double2 *__restrict__ P, long long ldp, const double2 *__restrict__ Q,
                                          long long ldq, const double *__restrict__ urow, int M, int N, int K, int i0,
                                          int j0, double (&acc1)[4][2][2][2], double (&acc2)[4][2][2][2],
@@ -89,6 +90,12 @@ __device__ __forceinline__ void tile_mma(const double2 *__restrict__ P, long lon
       for (int mt = 0; mt < 4; ++mt) a[mt] = sP[(kk + q) * PADS + wm * 32 + mt * 8 + g];
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) b[nt] = sQ[(kk + q) * PADS + wn * 16 + nt * 8 + g];
+      if (UQ) {
+        const int kg = kt * KT + kk + q;
+        const double u = (kg < K) ? urow[kg] : 0.0;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) b[nt] = make_double2(b[nt].x * u, b[nt].y * u);
+      }
       if (DUAL) {
         int kg = kt * KT + kk + q;
         double u = (kg < K) ? urow[kg] : 0.0;
@@ -177,9 +184,11 @@ __global__ void __launch_bounds__(NTHREADS) tapply_kernel(int dpad, int n_g, con
   store_tile(X + r0, ldw, dpad, n_g, blockIdx.x * MT, blockIdx.y * NT, acc, 0, 0);
 }
 
-// a4: one CTA per tile of the chosen triangle (linear index -> (bi, bj));
-// WITH_S false: H only (S is built in the Legendre form).
-template <bool WITH_S>
+// a4: one CTA per tile of the chosen triangle (linear index -> (bi, bj)).
+// MODE 0: H = W^H X and S = W^H diag(u) W (W = P, X = Q); MODE 1: H = P^H Q
+// only (S in the Legendre form, or H = Y^H Y of the HPD route); MODE 2:
+// S = P^H diag(u) P only, into H's pointer (the HPD route's S).
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS) hs_kernel(int n_g, int depth, const double2 *__restrict__ W,
                                                       const double2 *__restrict__ X, const double *__restrict__ urow,
                                                       long long ldw, double2 *__restrict__ H, double2 *__restrict__ S,
@@ -194,10 +203,11 @@ __global__ void __launch_bounds__(NTHREADS) hs_kernel(int n_g, int depth, const 
   if (!own.owns((long long)bi * MT, (long long)bj * NT)) return;  // 64 x 64 tiles lie inside one block
   double acc1[4][2][2][2], acc2[4][2][2][2];
   zero_acc<true>(acc1);
-  zero_acc<WITH_S>(acc2);
-  tile_mma<WITH_S>(W, ldw, X, ldw, urow, n_g, n_g, depth, bi * MT, bj * NT, acc1, acc2, smem);
+  zero_acc<MODE == 0>(acc2);
+  tile_mma<MODE == 0, MODE == 2>(W, ldw, MODE == 2 ? W : X, ldw, urow, n_g, n_g, depth, bi * MT, bj * NT, acc1, acc2,
+                                 smem);
   store_tile(H, ld, n_g, n_g, bi * MT, bj * NT, acc1, uplo, accumulate);
-  if (WITH_S) store_tile(S, ld, n_g, n_g, bi * MT, bj * NT, acc2, uplo, accumulate);
+  if (MODE == 0) store_tile(S, ld, n_g, n_g, bi * MT, bj * NT, acc2, uplo, accumulate);
 }
 
 // General C (+)= (+-) P^H Q (P: K x M, Q: K x N, C: M x N): one CTA per
@@ -256,26 +266,29 @@ cudaError_t launch_tapply_fp64(int dpad, int n_g, const double2 *T, const int *a
 
 cudaError_t launch_hs_fp64(int n_g, int depth, const double2 *W, const double2 *X, const double *urow, long long ldw,
                            double2 *H, double2 *S, long long ld, int uplo, int accumulate, const BlockOwner &own,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool gram) {
   if (n_g <= 0) return cudaSuccess;
   size_t sm = sizeof(double2) * 2 * 3 * KT * PADS;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(hs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(hs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(hs_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(hs_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(hs_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   long long nb = (n_g + MT - 1) / MT;
   long long ntiles = nb * (nb + 1) / 2;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (S)
-    hs_kernel<true><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate,
-                                                           own);
-  else
-    hs_kernel<false><<<(unsigned)ntiles, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate,
-                                                            own);
+  const unsigned g = (unsigned)ntiles;
+  if (gram) {  // H = X^H X (X = C^H W), then S = W^H diag(u) W
+    hs_kernel<1><<<g, NTHREADS, sm, s>>>(n_g, depth, X, X, urow, ldw, H, nullptr, ld, uplo, accumulate, own);
+    if (S) hs_kernel<2><<<g, NTHREADS, sm, s>>>(n_g, depth, W, W, urow, ldw, S, nullptr, ld, uplo, accumulate, own);
+  } else if (S) {
+    hs_kernel<0><<<g, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate, own);
+  } else {
+    hs_kernel<1><<<g, NTHREADS, sm, s>>>(n_g, depth, W, X, urow, ldw, H, S, ld, uplo, accumulate, own);
+  }
   return cudaGetLastError();
 }
 

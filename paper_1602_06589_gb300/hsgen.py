@@ -24,6 +24,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENUMERIC = range(7)
 FP64, SPLIT = 0, 1
 S_CONTRACTION, S_LEGENDRE = 0, 1
 SCHEME_AUTO, SCHEME_SLICES, SCHEME_MODULI = 0, 1, 2
+H_TW, H_HPD = 0, 1
 STATUS_NAMES = {0: "HSGEN_OK", 1: "HSGEN_EINVAL", 2: "HSGEN_ENOMEM", 3: "HSGEN_ECUDA", 4: "HSGEN_ETIMEOUT",
                 5: "HSGEN_ENOTSUP", 6: "HSGEN_ENUMERIC"}
 
@@ -34,7 +35,7 @@ _ip = C.POINTER(C.c_int)
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("target_rel_err", C.c_double), ("slices", C.c_int), ("uplo", C.c_int),
                 ("fill_full", C.c_int), ("atom_chunk", C.c_int), ("wait_timeout_ns", C.c_longlong),
-                ("s_form", C.c_int), ("scheme", C.c_int), ("moduli", C.c_int)]
+                ("s_form", C.c_int), ("scheme", C.c_int), ("moduli", C.c_int), ("h_form", C.c_int)]
 
 
 class TypeDesc(C.Structure):
@@ -52,12 +53,13 @@ class Stats(C.Structure):
                 ("ms_upload", C.c_double), ("ms_download", C.c_double), ("scheme", C.c_int), ("moduli", C.c_int),
                 ("bits", C.c_int), ("products", C.c_int), ("atom_chunks", C.c_int), ("tuned_rel_err", C.c_double),
                 ("stage_geometry", C.c_int), ("unit_order", C.c_int),
-                ("l2_hint", C.c_int)]
+                ("l2_hint", C.c_int), ("hpd_species", C.c_int)]
 
 
 EXPORTS = ["hsgen_default_options", "hsgen_create", "hsgen_set_atoms", "hsgen_build_HS", "hsgen_build_HS_blocks",
            "hsgen_build_HS_batched",
-           "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_depth_layout", "hsgen_autotune",
+           "hsgen_coefficients", "hsgen_coefficients_noalloc", "hsgen_T_matrix", "hsgen_T_factor", "hsgen_depth_layout",
+           "hsgen_autotune",
            "hsgen_reduce_generalized", "hsgen_get_stats", "hsgen_synchronize", "hsgen_last_error",
            "hsgen_destroy"]
 
@@ -94,6 +96,7 @@ def load(path: Optional[str] = None):
         lib.hsgen_coefficients.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
         lib.hsgen_coefficients_noalloc.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
         lib.hsgen_T_matrix.argtypes = [vp, C.c_int, _dp]
+        lib.hsgen_T_factor.argtypes = [vp, C.c_int, _dp, _ip]
         lib.hsgen_depth_layout.argtypes = [vp, _ip, C.c_int]
         lib.hsgen_autotune.argtypes = [vp, C.c_int, vp, vp, vp, C.c_longlong, vp]
         lib.hsgen_reduce_generalized.argtypes = [vp, C.c_int, vp, vp, C.c_longlong, vp]
@@ -221,6 +224,15 @@ def hsgen_T_matrix(ctx, type_index: int, nl: int) -> np.ndarray:
     return out.view(np.complex128).reshape(n, n, order="F")
 
 
+def hsgen_T_factor(ctx, type_index: int, n: int):
+    """(info, C): the Cholesky status of the species' T (0: HPD) and its lower
+    factor C (n x n, n = 2 N_L of the contraction's rows)."""
+    out = np.zeros(2 * n * n)
+    info = C.c_int(-1)
+    _check(ctx, load().hsgen_T_factor(ctx, int(type_index), out.ctypes.data_as(_dp), C.byref(info)), "hsgen_T_factor")
+    return int(info.value), out.view(np.complex128).reshape(n, n, order="F")
+
+
 def hsgen_depth_layout(ctx, n_atoms: int) -> np.ndarray:
     out = np.zeros(n_atoms + 1, dtype=np.int32)
     _check(ctx, load().hsgen_depth_layout(ctx, out.ctypes.data_as(_ip), n_atoms + 1), "hsgen_depth_layout")
@@ -263,7 +275,7 @@ class Generator:
     def __init__(self, system, device: int = 0, precision: int = FP64, slices: int = 0,
                  target_rel_err: float = 1e-12, uplo: str = "U", fill_full: bool = False, atom_chunk: int = 0,
                  wait_timeout_ns: int = 2_000_000_000, s_form: int = S_CONTRACTION, scheme: int = SCHEME_AUTO,
-                 moduli: int = 0):
+                 moduli: int = 0, h_form: int = H_TW):
         o = hsgen_default_options()
         o.precision = precision
         o.slices = slices
@@ -275,6 +287,7 @@ class Generator:
         o.s_form = s_form
         o.scheme = scheme
         o.moduli = moduli
+        o.h_form = h_form
         self.device = device
         self.system = system
         self.ctx = hsgen_create(device, o)
@@ -367,6 +380,10 @@ class Generator:
 
     def T_matrix(self, type_index: int) -> np.ndarray:
         return hsgen_T_matrix(self.ctx, type_index, self.system.types[type_index].nl)
+
+    def T_factor(self, type_index: int, nl: Optional[int] = None):
+        """(info, C) of hsgen_T_factor; nl: N_L of the contraction's rows (default the species' N_L)."""
+        return hsgen_T_factor(self.ctx, type_index, 2 * (nl or self.system.types[type_index].nl))
 
     def stats(self) -> dict:
         return hsgen_get_stats(self.ctx)
