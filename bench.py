@@ -281,7 +281,8 @@ def run_batched(args, w, world, rank, local, dist):
     stream = torch.cuda.current_stream(dev)
     s_form = hsgen.S_LEGENDRE if args.s_form == "legendre" else hsgen.S_CONTRACTION
     g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form,
-                        target_rel_err=args.target, scheme=SCHEMES[args.scheme], moduli=args.moduli)
+                        target_rel_err=args.target, scheme=SCHEMES[args.scheme], moduli=args.moduli,
+                        h_form=hsgen.H_HPD if args.h_form == "hpd" else hsgen.H_TW)
     kv_host = [np.ascontiguousarray(w.kvecs[k]) for k in mine]
     Hs = [torch.zeros((n, n), dtype=torch.complex128, device=dev) for n in n_gs]
     Ss = [torch.zeros_like(h) for h in Hs]
@@ -660,6 +661,12 @@ def main():
                     help="skip hsgen_autotune before the warm-up (split form)")
     ap.add_argument("--s-form", choices=["contraction", "legendre"], default="contraction",
                     help="S as the A^H A + B^H U B contraction (default) or in the m-summed Legendre form")
+    ap.add_argument("--h-form", choices=["tw", "hpd"], default="tw",
+                    help="H as W^H (T W) for every species (default) or by the HPD route (Sec. 4.6.2-4.6.3: "
+                         "species whose T passes the Cholesky test take Y = C^H W and H = Y^H Y)")
+    ap.add_argument("--shift-energies", type=float, default=0.0,
+                    help="raise every E_l of the synthetic radial data by this much (12 makes every species' "
+                         "T positive definite)")
     ap.add_argument("--library-bars", action="store_true",
                     help="time cuBLAS ZGEMM + ZHERK (FP64 and FP64-emulated) beside the split form, then exit")
     ap.add_argument("--bar-reps", type=int, default=1)
@@ -671,6 +678,10 @@ def main():
     from workloads import make_config
 
     w = make_config(args.config, n_g_override=args.n_g or None)
+    if args.shift_energies:
+        from workloads import shift_energies
+
+        w.system = shift_energies(w.system, args.shift_energies)
     if args.l_nonsph >= 0:  # T's non-spherical part only for l, l' <= l_nonsph (Fig. Tmat_structure)
         for ty in w.system.types:
             ty.lmax_nonsph = min(args.l_nonsph, ty.lmax)
@@ -722,7 +733,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     s_form = hsgen.S_LEGENDRE if args.s_form == "legendre" else hsgen.S_CONTRACTION
     g = hsgen.Generator(sysm, device=local, precision=precision, slices=args.slices, s_form=s_form,
-                        target_rel_err=args.target, scheme=SCHEMES[args.scheme], moduli=args.moduli)
+                        target_rel_err=args.target, scheme=SCHEMES[args.scheme], moduli=args.moduli,
+                        h_form=hsgen.H_HPD if args.h_form == "hpd" else hsgen.H_TW)
     kv = torch.from_numpy(kv_host).to(dev)
     H = torch.zeros((n, n), dtype=torch.complex128, device=dev)
     S = torch.zeros_like(H)
@@ -801,11 +813,14 @@ def main():
                    "s_form": "legendre (Eq. overlap_no_m, FP64)" if st.get("s_form") == hsgen.S_LEGENDRE
                    else "contraction",
                    "l_nonsph": args.l_nonsph if args.l_nonsph >= 0 else "l_max",
+                   "h_form": ({"route": "hpd", "species_routed": st.get("hpd_species", 0)}
+                              if args.h_form == "hpd" else "tw"),
+                   "energy_shift": args.shift_energies,
                    "slices": st["slices"] if precision == hsgen.SPLIT else None,
                    "scheme": ({1: "slices (Ozaki I)", 2: "moduli (Ozaki II)"}.get(st["scheme"])
                               if precision == hsgen.SPLIT else None),
                    "moduli": st["moduli"] if precision == hsgen.SPLIT else None,
-                   "operand_bits": st["bits"] if precision == hsgen.SPLIT else None,
+                   "operand_column_norm_bits": st["bits"] if precision == hsgen.SPLIT else None,
                    "bf16_products_per_fp64_product": st["products"] if precision == hsgen.SPLIT else None,
                    "target_rel_err": args.target if precision == hsgen.SPLIT else None,
                    "atom_chunks": st["atom_chunks"],

@@ -81,9 +81,9 @@ enum { HSGEN_S_CONTRACTION = 0, HSGEN_S_LEGENDRE = 1 };
  * counterpart in the paper, which is all FP64):
  *  HSGEN_SCHEME_SLICES: s slices per operand, s(s+1)/2 products (Ozaki
  *    scheme I);
- *  HSGEN_SCHEME_MODULI: operands rounded to b-bit integers, one product per
- *    modulus, exact integer result by the Chinese remainder theorem (Ozaki
- *    scheme II), 10..14 moduli;
+ *  HSGEN_SCHEME_MODULI: every operand column rounded to integers of 2-norm
+ *    at most 2^B, one product per modulus, exact integer result by the
+ *    Chinese remainder theorem (Ozaki scheme II), 10..14 moduli;
  *  HSGEN_SCHEME_AUTO: moduli when a count of at most 14 meets target_rel_err
  *    (and no slice count is forced), otherwise slices. */
 enum { HSGEN_SCHEME_AUTO = 0, HSGEN_SCHEME_SLICES = 1, HSGEN_SCHEME_MODULI = 2 };
@@ -171,7 +171,8 @@ typedef struct {
   int scheme;              /* split form of the last pass: HSGEN_SCHEME_SLICES  */
                            /* or HSGEN_SCHEME_MODULI                            */
   int moduli;              /* moduli used (moduli scheme)                       */
-  int bits;                /* integer bits per operand (moduli scheme)          */
+  int bits;                /* moduli scheme: B, the operand columns' integer    */
+                           /* 2-norm bound 2^B                                  */
   int products;            /* BF16 products per FP64 product of the contraction */
   int atom_chunks;         /* passes over the atoms (a6) of the last build      */
   double tuned_rel_err;    /* hsgen_autotune: relative Frobenius error of the   */

@@ -1216,12 +1216,17 @@ __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ 
   }
 }
 
-// Moduli form: residues of the b-bit integers N = round(v 2^(b - e)) (one
-// scale 2^e per column) for every modulus, balanced to |r| <= 128, as BF16
+// Moduli form: residues of the integers N = round(v 2^f), with one power of
+// two 2^f per column chosen from the column's 2-norm: f is the largest value
+// with 2^f ||v|| (1 + 1e-9) + 0.5 sqrt(2K) <= 2^B, so the rounded column has
+// ||N||_2 <= 2^B (every part is off by at most 1/2; the factor covers the
+// rounding of the norm). The column's exponent e = B - f is stored (v ~ N
+// 2^(e - B), as with a scale from the column's largest entry). For every
+// modulus the balanced residues |r| <= 128, exact in BF16, are written as BF16
 // planes in the k-blocked layout of slice_kernel; plane i * planes + {0, 1, 2}
-// holds re, im, -re of modulus i. |N| < 2^48 is cut into four 12-bit pieces,
-// exact in FP32, so |N| mod m = sum_j piece_j (2^12j mod m) mod m is formed
-// in FP32 (every partial sum is an integer below 2^22, exact) with a
+// holds re, im, -re of modulus i. |N| <= 2^B <= 2^47 is cut into four 12-bit
+// pieces, exact in FP32, so |N| mod m = sum_j piece_j (2^12j mod m) mod m is
+// formed in FP32 (every partial sum is an integer below 2^22, exact) with a
 // quotient rounded by the 1.5 2^23 shift: full-rate FP32 work, no integer
 // division and no conversion instruction. Each thread takes two consecutive
 // depth rows (one 4-byte store per plane).
@@ -1235,20 +1240,24 @@ __global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict_
   const double2 *c = src + (size_t)col * lds;
   __shared__ double red[8];
   __shared__ int e_sh;
-  double mx = 0.0;
+  double ss = 0.0;  // sum of squares of the (weighted) column
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double2 v = c[k];
     const double u = urow ? urow[k] : 1.0;
-    mx = fmax(mx, fmax(fabs(v.x * u), fabs(v.y * u)));
+    ss = fma(v.x * u, v.x * u, fma(v.y * u, v.y * u, ss));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    const int e = (m > 0.0) ? ilogb(m) + 1 : 0;
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    int e = 0;
+    if (t > 1e-280) {  // below: a zero column (or one that rounds to zero at any usable scale)
+      const double room = ldexp(1.0, b) - 0.5 * sqrt(2.0 * (double)K);
+      e = b - ilogb(room / (sqrt(t) * (1.0 + 1e-9)));
+    }
     e_sh = e;
     expo[col] = e;
   }
@@ -1427,28 +1436,33 @@ cudaError_t launch_residue(const double2 *src, long long lds, int K, const doubl
 // pairwise coprime moduli <= 256 (2^8, 3.5.17, 11.23, 251, 13.19, then primes
 // and 7.31), largest first: n of them give M = prod m_i of about 7.9 n bits
 constexpr int kModuli[kMaxModuli] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199};
-// error model of the moduli form (relative Frobenius error of H and S for
-// b-bit operands): kCrtErr 2^-b; measured 2.3-2.5 x 2^-b for b = 35..43,
-// so the model keeps a factor ~3 of margin
-constexpr double kCrtErr = 8.0;
+// A-priori error model of the moduli form (relative Frobenius error of H
+// and S for columns scaled to 2-norm 2^B, depth K): kCrtErr sqrt(2K) 2^-B,
+// the worst case of columns whose entries are all of one size (each then
+// keeps B - log2(sqrt(2K)) bits; measured 2.3-2.5 x 2^-bits with a scale from
+// the largest entry), with a little margin. Coefficient columns hold their
+// norm in a few large entries and do much better: 1.1e-11 at B = 39 on the
+// one-atom workload (K = 50), and for W^H (T W) at K = 30976 (a numpy
+// emulation of the rounding) 2.6e-11, 1.6e-12, 2.1e-13 for B = 39, 43, 46,
+// 0.06 sqrt(2K) 2^-B. hsgen_autotune measures instead of using the model.
+constexpr double kCrtErr = 3.0;
 
 unsigned __int128 crt_M(int n) {
   unsigned __int128 M = 1;
-  for (int i = 0; i < n; ++i) M *= (unsigned)kModuli[i];
+  for (int i = 0; i < n; ++i) M *= (unsigned __int128)kModuli[i];
   return M;
 }
 
-// The largest b with 4 K 2^(2b) < M (K: complex depth), at most 47: then
-// |C'| <= 2 K 2^(2b) < M / 2 for b-bit operands, so C' is recovered exactly.
-int crt_bits(int n, long long K) {
+// Norm bits B of n moduli: the largest B <= 47 with 2^(2B+1) < M. With both
+// operands' columns of 2-norm <= 2^B, every real and imaginary part of the
+// integer product is a dot product of two real vectors of those norms, so
+// |C'| <= 2^(2B) < M / 2 (Cauchy-Schwarz) and C' is the balanced
+// representative of its residues (Chinese remainder theorem). 47 keeps every
+// |N| <= 2^47 within the residue kernel's four 12-bit pieces.
+int crt_bits(int n) {
   const unsigned __int128 M = crt_M(n);
-  const unsigned __int128 k4 = (unsigned __int128)(4 * std::max(K, 1LL));
   int b = 0;
-  while (b < 47) {
-    const int sh = 2 * (b + 1);
-    if (sh > 120 || (k4 << sh) >> sh != k4 || (k4 << sh) >= M) break;
-    ++b;
-  }
+  while (b < 47 && ((unsigned __int128)1 << (2 * (b + 1) + 1)) < M) ++b;
   return b;
 }
 
@@ -1753,7 +1767,8 @@ CrtWs crt_ws_layout(void *base, int n_g, int depth, int nmod, long long slots) {
 int choose_moduli(double target_rel_err, int override_moduli, long long K) {
   if (override_moduli > 0) return std::max(kMinModuli, std::min(override_moduli, kMaxModuli));
   for (int n = kMinModuli; n <= kMaxModuli; ++n)
-    if (kCrtErr * std::ldexp(1.0, -crt_bits(n, K)) <= target_rel_err) return n;
+    if (kCrtErr * std::sqrt(2.0 * (double)std::max(K, 1LL)) * std::ldexp(1.0, -crt_bits(n)) <= target_rel_err)
+      return n;
   return 0;
 }
 
@@ -1770,7 +1785,7 @@ SplitPlan split_plan(const hsgen_ctx *ctx, int depth) {
     if (n > 0) {
       p.scheme = kSchemeModuli;
       p.nmod = n;
-      p.bits = crt_bits(n, depth);
+      p.bits = crt_bits(n);
     }
   }
   return p;
