@@ -125,7 +125,7 @@ class ClockSampler:
         return out
 
 
-def _traffic(config: int, kseg: int, scheme: int):
+def _traffic(config: int, st: dict):
     """DRAM bytes per H/S depth-segment launch of the moduli kernel from the
     committed ncu record, or None when the record is for another workload,
     schedule or form, or the kernel's source has changed since."""
@@ -145,7 +145,9 @@ def _traffic(config: int, kseg: int, scheme: int):
     except ValueError:
         return None
     sha = hashlib.sha256(src[a:b].encode()).hexdigest()
-    if config != 4 or kseg != 32 or scheme != 2 or rec.get("kernel_source_sha256") != sha:
+    same = config == 4 and st.get("scheme") == 2 and rec.get("kernel_source_sha256") == sha and all(
+        st.get(k) == rec.get(k) for k in ("kseg_blocks", "tile_band", "unit_order", "l2_hint", "moduli"))
+    if not same:
         return None
     return rec["dram_bytes_read"] + rec["dram_bytes_write"], rec["algorithmic_bytes"]
 
@@ -602,7 +604,7 @@ def roofline(st, f_contract, c_ms, precision, peaks, clk_s, args, hsgen):
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         pmhz = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
         peak_clk = peak * mhz / pmhz if (mhz and pmhz) else peak
-        tr = _traffic(args.config, st.get("kseg_blocks", 0), scheme) \
+        tr = _traffic(args.config, st) \
             if not args.n_g and st.get("s_form") != hsgen.S_LEGENDRE else None
         return {"bound": "tensor", "achieved": achieved, "peak": peak_clk, "unit": "TFLOP/s",
                 "frac": achieved / peak_clk, "frac_vs_measured_peak": achieved / peak,
@@ -890,10 +892,19 @@ def main():
             t = torch.tensor([te], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
+        # after the timed calls: this box's device-to-pinned-host copy rate (one
+        # 6.4 GB copy of H), which bounds how fast the copy-out can keep pace
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        Hh.copy_(H, non_blocking=True)
+        c1.record(stream)
+        c1.synchronize()
+        d2h = H.numel() * 16 / (c0.elapsed_time(c1) * 1e-3) / 1e9
         line["e2e"] = {"value": te / world, "unit": "s/k-point", "h2d_bytes_per_step": int(kh.numel() * 8),
                        "d2h_bytes_per_step": int(2 * n * n * 16),
                        "calls_s": [round(x, 4) for x in walls], "device_ms": [round(x, 1) for x in dev_ms],
-                       "upload_ms": [round(x, 1) for x in up_ms], "download_ms": [round(x, 1) for x in down_ms]}
+                       "upload_ms": [round(x, 1) for x in up_ms], "download_ms": [round(x, 1) for x in down_ms],
+                       "d2h_copy_gbps": round(d2h, 1)}
         del Hh, Sh
 
     # accuracy of the timed build (after the timed region): whole columns vs the oracle
