@@ -45,6 +45,9 @@
  *  HSGEN_CRT_ORDER     0 or 1, the order of the moduli kernel's work units;
  *  HSGEN_L2_HINT       0 or 8, the L2 priority of its operand loads;
  *  HSGEN_CRT_GEOMETRY  0 or 1, its pipeline stage geometry;
+ *  HSGEN_CRT_RECON     1 (default): the moduli form's reconstruction of H
+ *                      and S in a kernel of its own, 0: inside the
+ *                      contraction's last launch;
  *  HSGEN_WS_BYTES      the split form's workspace budget, which sets the
  *                      passes over the atoms when opt.atom_chunk is 0
  *                      (default 176e9);

@@ -227,6 +227,7 @@ hsgen_status hsgen_create(hsgen_ctx **out, int cuda_device, const hsgen_options 
   if (const char *co = std::getenv("HSGEN_CRT_ORDER")) ctx->crt_order = std::atoi(co) == 1 ? 1 : 0;
   if (const char *tb = std::getenv("HSGEN_TILE_BAND")) ctx->tile_band = std::max(1, std::atoi(tb));
   if (const char *lh = std::getenv("HSGEN_L2_HINT")) ctx->l2_hint = std::atoi(lh) & 15;
+  if (const char *rc = std::getenv("HSGEN_CRT_RECON")) ctx->crt_recon_apart = std::atoi(rc) == 0 ? 0 : 1;
   if (cudaSetDevice(cuda_device) != cudaSuccess || upload_tables() != cudaSuccess ||
       split_upload_tables() != cudaSuccess) {
     delete ctx;

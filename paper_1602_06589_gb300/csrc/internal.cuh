@@ -134,6 +134,7 @@ struct hsgen_ctx {
   int crt_geom = 0;                 // moduli kernel's stage geometry (0: 3 x 2 k-blocks, 1: 2 x 3)
   int crt_order = 1;                // moduli kernel's unit order (0: tile-major, 1: modulus-major)
   int l2_hint = 8;                  // moduli kernel's L2 priorities of its A and B loads (8: B evict-last)
+  int crt_recon_apart = 1;          // moduli form: reconstruction in a kernel of its own (0: in the contraction)
   std::vector<int2> tiles_host;     // host copy of that list (column bands of the overlapped copies)
   cudaStream_t copy_stream = nullptr;  // host outputs: copies of finished column bands
   cudaEvent_t copy_ev = nullptr;       // orders each copy after the launch that finished its bands

@@ -146,6 +146,7 @@ struct GemmParams {
   CrtConsts crt;  // moduli form only
   int crt_order;  // moduli form: 0 tile-major units, 1 modulus-major (see crt_unit)
   int l2_hint;    // moduli form: L2 priority of A (bits 0-1) and B (bits 2-3) loads: 0 normal, 1 first, 2 last
+  int recon_apart;  // moduli form: the launch that ends the depth leaves the reconstruction to crt_reconstruct_kernel
 };
 
 // ---------------------------------------------------------------------------
@@ -813,6 +814,70 @@ __device__ __forceinline__ int mod_small(int a, int m, float inv_m) {
   return r;
 }
 
+// One entry of the moduli form from its residues (byte b of word q of each
+// modulus's 16-byte group): C' = sum_i r_i c_i mod M in 32-bit limbs (one
+// 32 x 32 -> 64-bit multiply-add per limb and modulus; each limb sum < 2^44),
+// the quotient by M (< 2^12) estimated from the high word and corrected once,
+// the balanced representative, then |C'| 2^e as a double built from its bits
+// (the top 53 bits, rounded half up on the next one; integer work only).
+__device__ __forceinline__ double crt_value(const uint4 (&rv)[kMaxModuli], int NM, int q, int b, const CrtConsts &c,
+                                            int e) {
+  unsigned long long L0 = 0, L1 = 0, L2 = 0, L3 = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxModuli; ++i) {
+    if (i >= NM) break;
+    const uint32_t word = (q == 0) ? rv[i].x : (q == 1) ? rv[i].y : (q == 2) ? rv[i].z : rv[i].w;
+    const uint32_t r = (word >> (8 * b)) & 0xFFu;
+    L0 += (unsigned long long)r * (uint32_t)c.c_lo[i];
+    L1 += (unsigned long long)r * (uint32_t)(c.c_lo[i] >> 32);
+    L2 += (unsigned long long)r * (uint32_t)c.c_hi[i];
+    L3 += (unsigned long long)r * (uint32_t)(c.c_hi[i] >> 32);
+  }
+  L1 += L0 >> 32;
+  L2 += L1 >> 32;
+  L3 += L2 >> 32;  // the sum is below 14 x 255 x M < 2^123
+  unsigned __int128 sum = ((unsigned __int128)((L3 << 32) | (uint32_t)L2) << 64) | ((L1 << 32) | (uint32_t)L0);
+  const float qf = (float)((L3 << 32) | (uint32_t)L2) * c.q_scale - 0.5f;
+  const uint32_t q0 = qf > 0.f ? (uint32_t)qf : 0u;
+  {
+    unsigned long long t = (unsigned long long)q0 * (uint32_t)c.M_lo;
+    const uint32_t p0 = (uint32_t)t;
+    t = (t >> 32) + (unsigned long long)q0 * (uint32_t)(c.M_lo >> 32);
+    const uint32_t p1 = (uint32_t)t;
+    t = (t >> 32) + (unsigned long long)q0 * (uint32_t)c.M_hi;
+    const uint32_t p2 = (uint32_t)t;
+    t = (t >> 32) + (unsigned long long)q0 * (uint32_t)(c.M_hi >> 32);
+    sum -= ((unsigned __int128)((t << 32) | p2) << 64) | (((unsigned long long)p1 << 32) | p0);
+  }
+  const unsigned __int128 Mv = ((unsigned __int128)c.M_hi << 64) | c.M_lo;
+  const unsigned __int128 Mh = ((unsigned __int128)c.Mh_hi << 64) | c.Mh_lo;
+  if (sum >= Mv) sum -= Mv;
+  const bool neg = sum > Mh;
+  const unsigned __int128 mag = neg ? Mv - sum : sum;
+  const unsigned long long mh = (unsigned long long)(mag >> 64), ml = (unsigned long long)mag;
+  if (!(mh | ml)) return 0.0;
+  const int nb = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);  // bit length
+  const int sh = nb - 54;                                                          // keep 54 bits
+  unsigned long long top;
+  if (sh <= 0)
+    top = ml << (-sh);
+  else if (sh < 64)
+    top = (ml >> sh) | (mh << (64 - sh));
+  else
+    top = mh >> (sh - 64);
+  unsigned long long mant = (top + 1) >> 1;  // 53 bits, or 2^53 after rounding up
+  int ex = nb - 1 + e;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  double x = (ex > -1023 && ex < 1024)
+                 ? __longlong_as_double((long long)(((unsigned long long)(ex + 1023) << 52) |
+                                                    (mant & 0xFFFFFFFFFFFFFull)))
+                 : ldexp((double)mant, ex - 52);
+  return neg ? -x : x;
+}
+
 // The work of a CTA pair is its tiles t = pair, pair + npairs, .. times the
 // n moduli, in units (modulus i, tile t). Tile-major order (0) runs every
 // modulus of a tile before its next tile, so the operands a wave of tiles
@@ -997,7 +1062,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     // ------------------------------ epilogue ----------------------------------
     // Warp w: TMEM lane quadrant w % 4 (rows), accumulator half hf = w / 4
     // (hf 0: real parts, hf 1: imaginary parts of the tile's 128 columns);
-    // each thread holds the int32 sums of its row's 128 values.
+    // each thread holds the int32 sums of its row's 128 values. (Giving each
+    // thread the real and imaginary parts of 64 columns, for 16-byte stores
+    // of whole entries, made the launch that reconstructs H and S slower.)
     const int qd = warp & 3;
     const int hf = warp >> 2;
     const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
@@ -1075,54 +1142,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         }
       }
       if (!ok) break;
-      if (!pr.seg_last || i != NM - 1) continue;
-      // ---- last segment: C' from its residues (CRT), scaled to FP64 by 2^(eA + eB - 2b)
+      if (!pr.seg_last || i != NM - 1 || P.recon_apart) continue;
+      // ---- last segment: C' from its residues (CRT), scaled to FP64 by 2^(eA + eB - 2B)
       const int row = ti.m0 + (int)rank * BM + qd * 32 + lane;
       if (row >= pr.M) continue;
       const int eA = pr.expA[row];
       double *Cd = (double *)pr.C + 2 * (long long)row + hf;
-      const unsigned __int128 Mv = ((unsigned __int128)P.crt.M_hi << 64) | P.crt.M_lo;
-      const unsigned __int128 Mh = ((unsigned __int128)P.crt.Mh_hi << 64) | P.crt.Mh_lo;
       for (int g = 0; g < 8; ++g) {
         uint4 rv[kMaxModuli];
 #pragma unroll
         for (int i = 0; i < kMaxModuli; ++i)
           if (i < NM) rv[i] = res_ptr(i)[g];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int u = g * 16 + q * 4 + b;
-            const int col = ti.n0 + u;
-            const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
-            if (!keep) continue;
-            unsigned __int128 sum = 0;
-#pragma unroll
-            for (int i = 0; i < kMaxModuli; ++i) {
-              if (i >= NM) break;
-              const uint32_t word = (q == 0) ? rv[i].x : (q == 1) ? rv[i].y : (q == 2) ? rv[i].z : rv[i].w;
-              const unsigned long long r = (word >> (8 * b)) & 0xFFu;
-              sum += (unsigned __int128)(r * P.crt.c_lo[i]) + ((unsigned __int128)__umul64hi(r, P.crt.c_lo[i]) << 64) +
-                     ((unsigned __int128)(r * P.crt.c_hi[i]) << 64);
-            }
-            // sum mod M: quotient estimated from the high word, then corrected
-            const float qf = (float)(unsigned long long)(sum >> 64) * P.crt.q_scale - 0.5f;
-            const unsigned long long q0 = qf > 0.f ? (unsigned long long)qf : 0ull;
-            sum -= (unsigned __int128)q0 * Mv;
-            if (sum >= Mv) sum -= Mv;
-            const bool neg = sum > Mh;
-            const unsigned __int128 mag = neg ? Mv - sum : sum;
-            double x = fma((double)(unsigned long long)(mag >> 64), 18446744073709551616.0,
-                           (double)(unsigned long long)mag);
-            const int e = eA + pr.expB[col] - pr.F;
-            const double scl =
-                (e > -1022 && e < 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
-            x = (neg ? -x : x) * scl;
-            double *dst = Cd + 2 * (size_t)col * pr.ldc;
-            if (pr.accumulate) x += *dst;
-            if (hf == 1 && pr.uplo && row == col) x = 0.0;
-            *dst = x;
-          }
+        for (int u = 0; u < 16; ++u) {
+          const int col = ti.n0 + g * 16 + u;
+          const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
+          if (!keep) continue;
+          double x = crt_value(rv, NM, u >> 2, u & 3, P.crt, eA + pr.expB[col] - pr.F);
+          double *dst = Cd + 2 * (size_t)col * pr.ldc;
+          if (pr.accumulate) x += *dst;
+          if (hf == 1 && pr.uplo && row == col) x = 0.0;
+          *dst = x;
+        }
       }
     }
   } else {
@@ -1133,6 +1174,45 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
   cluster_sync();
   tc_fence_after();
   if (warp == WARP_MMA) tc_dealloc(tbase, TMEM_COLS);
+}
+
+// The reconstruction of the moduli form as a kernel of its own, after the
+// launch that ends the depth (same parameters): block (t, rank, g) takes the
+// 16 columns [16 g, 16 g + 16) of tile t's rows [128 rank, 128 rank + 128);
+// thread (warp w, lane) is the thread of the contraction's epilogue that
+// stored the residues of row 32 (w % 4) + lane, part w / 4 (real, imaginary).
+// With many blocks per SM the loads of the residues and of H, S overlap,
+// where the contraction's eight epilogue warps would leave the MMA waiting.
+__global__ void __launch_bounds__(256) crt_reconstruct_kernel(const __grid_constant__ GemmParams P) {
+  const long long t = blockIdx.x;
+  const int rank = blockIdx.y, g = blockIdx.z;
+  long long slot;
+  const Tile ti = decode_tile_crt(P, t, slot);
+  const GemmProblem &pr = problem(P, ti.prob);
+  if (!pr.seg_last) return;
+  const int NM = P.crt.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int qd = warp & 3, hf = warp >> 2;
+  const int row = ti.m0 + rank * BM + qd * 32 + lane;
+  if (row >= pr.M) return;
+  const int eA = pr.expA[row];
+  double *Cd = (double *)pr.C + 2 * (long long)row + hf;
+  uint4 rv[kMaxModuli];
+#pragma unroll
+  for (int i = 0; i < kMaxModuli; ++i)
+    if (i < NM)
+      rv[i] = ((const uint4 *)(pr.res + ((((size_t)slot * NM + i) * 2 + rank) * 256 + threadIdx.x) * 128))[g];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int col = ti.n0 + g * 16 + u;
+    const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
+    if (!keep) continue;
+    double x = crt_value(rv, NM, u >> 2, u & 3, P.crt, eA + pr.expB[col] - pr.F);
+    double *dst = Cd + 2 * (size_t)col * pr.ldc;
+    if (pr.accumulate) x += *dst;
+    if (hf == 1 && pr.uplo && row == col) x = 0.0;
+    *dst = x;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1412,7 +1492,9 @@ cudaError_t launch_gemm(GemmParams &P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_crt(GemmParams &P, int geom, cudaStream_t s) {
+// last_seg: some problem of this launch ends the depth (its tiles are then
+// reconstructed by crt_reconstruct_kernel when P.recon_apart is set).
+cudaError_t launch_crt(GemmParams &P, int geom, cudaStream_t s, bool last_seg) {
   cudaError_t e = gemm_attrs();
   if (e != cudaSuccess) return e;
   if (P.ntiles <= 0) return cudaSuccess;
@@ -1421,6 +1503,10 @@ cudaError_t launch_crt(GemmParams &P, int geom, cudaStream_t s) {
     crt_gemm_kernel<3, 2, 6><<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
   else
     crt_gemm_kernel<2, 3, 8><<<(unsigned)(2 * pairs), NTHREADS, SMEM_BYTES, s>>>(P);
+  if (P.recon_apart && last_seg) {
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    crt_reconstruct_kernel<<<dim3((unsigned)P.ntiles, 2, BNC / 16), 256, 0, s>>>(P);
+  }
   return cudaGetLastError();
 }
 
@@ -2065,11 +2151,12 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
         P.crt = cc;
         P.crt_order = ctx->crt_order;
         P.l2_hint = ctx->l2_hint;
+        P.recon_apart = ctx->crt_recon_apart;
         if (!crt_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, nkb_all, accumulate, uplo, cw.Wr, cw.Xr,
                           cw.Yr, cw.expW, cw.expX, cw.expY, H, S, ld, (const int2 *)ctx->d_tiles + t0, cnt, 0, t0,
                           slots, cw.store, pl.nmod, pl.bits, gram))
           return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S, moduli)");
-        HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s));
+        HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s, kb0 + seg >= nkb_all));
         return HSGEN_OK;
       }
       if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
@@ -2466,7 +2553,8 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
             P.crt = cc;
             P.crt_order = ctx->crt_order;
             P.l2_hint = ctx->l2_hint;
-            HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s));
+            P.recon_apart = ctx->crt_recon_apart;
+            HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s, sg == nseg - 1));
           } else {
             HSG_LAUNCH(ctx, launch_gemm(P, s));
           }

@@ -168,13 +168,16 @@ def test_moduli_stage_geometries_and_unit_orders_agree_bitwise(hs, monkeypatch):
     """The moduli kernel's two stage geometries (3 stages of 2 k-blocks with
     chunks of 8, 2 stages of 3 with chunks of 6), its two orders of
     (tile, modulus) units and its L2 priorities sum the same exact integers,
-    so H and S agree bit for bit."""
+    and the reconstruction inside the contraction or in a kernel of its own
+    is the same arithmetic, so H and S agree bit for bit."""
     w = make_config(1)
     out = []
-    for geom, order, hint in (("0", "0", "0"), ("1", "0", "8"), ("0", "1", "0"), ("1", "1", "8")):
+    for geom, order, hint, recon in (("0", "0", "0", "1"), ("1", "0", "8", "0"), ("0", "1", "0", "0"),
+                                     ("1", "1", "8", "1")):
         monkeypatch.setenv("HSGEN_CRT_GEOMETRY", geom)
         monkeypatch.setenv("HSGEN_CRT_ORDER", order)
         monkeypatch.setenv("HSGEN_L2_HINT", hint)
+        monkeypatch.setenv("HSGEN_CRT_RECON", recon)
         H, S, st = run_gpu(hs, w.system, w.kvecs[0], scheme=hs.SCHEME_MODULI)
         assert st["stage_geometry"] == int(geom) and st["unit_order"] == int(order) and st["l2_hint"] == int(hint)
         out.append((H, S))
@@ -262,6 +265,31 @@ def test_split_complex_T_override(hs, scheme):
     kv = kpoint_list(sysm.lattice, (0.1, 0.0, 0.2), 140)
     H, S, _ = run_gpu(hs, sysm, kv, **scheme_kw(hs, scheme))
     check(sysm, kv, H, S)
+
+
+@pytest.mark.parametrize("n_moduli", [10, 14])
+def test_moduli_at_the_cauchy_schwarz_bound(hs, n_moduli):
+    """The moduli form's integer product is exact because every operand
+    column is rounded to integers of 2-norm <= 2^B with 2^(2B+1) < M, and
+    |P'^H Q'| <= ||P'|| ||Q'|| (Cauchy-Schwarz). With T = 1 the diagonal of
+    H = W^H W reaches that bound (H_jj = ||w_j||^2, both factors the same
+    column), so a bound one bit too loose would wrap H's diagonal modulo M;
+    S = W^H U W has its diagonal near it as well."""
+    w = make_config(1)
+    sysm = w.system
+    for ty in sysm.types:
+        ty.T_override = np.eye(2 * ty.nl, dtype=complex)
+    kv = w.kvecs[0][:1500]
+    H, S, st = run_gpu(hs, sysm, kv, scheme=hs.SCHEME_MODULI, moduli=n_moduli)
+    assert st["moduli"] == n_moduli
+    Ho, So = oracle.build_HS(sysm, kv, full=True)
+    d, do = np.diag(H).real, np.diag(Ho).real
+    assert np.all(do > 0)
+    assert np.max(np.abs(d - do) / do) <= 1e-9, np.max(np.abs(d - do) / do)  # a wrap would be off by ~M
+    # the rounding error itself, within the a-priori model 3 sqrt(2K) 2^-B
+    depth = sum(2 * sysm.types[t].nl for t in sysm.type_of_atom)
+    (hf, _), (sf, _), _ = errors(sysm, kv, H, S)
+    assert max(hf, sf) <= 3.0 * np.sqrt(2 * depth) * 2.0 ** -st["bits"] + 2e-13, (hf, sf, st["bits"])
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
