@@ -145,11 +145,13 @@ def _traffic(config: int, st: dict):
     except ValueError:
         return None
     sha = hashlib.sha256(src[a:b].encode()).hexdigest()
-    same = config == 4 and st.get("scheme") == 2 and rec.get("kernel_source_sha256") == sha and all(
-        st.get(k) == rec.get(k) for k in ("kseg_blocks", "tile_band", "unit_order", "l2_hint", "moduli"))
-    if not same:
+    if config != 4 or st.get("scheme") != 2:
         return None
-    return rec["dram_bytes_read"] + rec["dram_bytes_write"], rec["algorithmic_bytes"]
+    for r in (rec if isinstance(rec, list) else [rec]):  # one record per schedule captured
+        if r.get("kernel_source_sha256") == sha and all(
+                st.get(k) == r.get(k) for k in ("kseg_blocks", "tile_band", "unit_order", "l2_hint", "moduli")):
+            return r["dram_bytes_read"] + r["dram_bytes_write"], r["algorithmic_bytes"]
+    return None
 
 
 # whole columns of the triangle compared with the oracle after the timed

@@ -823,6 +823,7 @@ __device__ __forceinline__ int mod_small(int a, int m, float inv_m) {
 __device__ __forceinline__ double crt_value(const uint4 (&rv)[kMaxModuli], int NM, int q, int b, const CrtConsts &c,
                                             int e) {
   unsigned long long L0 = 0, L1 = 0, L2 = 0, L3 = 0;
+  const bool limb3 = (c.M_hi >> 32) != 0;  // M < 2^96 (up to 12 moduli): every c_i's fourth limb is 0
 #pragma unroll
   for (int i = 0; i < kMaxModuli; ++i) {
     if (i >= NM) break;
@@ -831,7 +832,7 @@ __device__ __forceinline__ double crt_value(const uint4 (&rv)[kMaxModuli], int N
     L0 += (unsigned long long)r * (uint32_t)c.c_lo[i];
     L1 += (unsigned long long)r * (uint32_t)(c.c_lo[i] >> 32);
     L2 += (unsigned long long)r * (uint32_t)c.c_hi[i];
-    L3 += (unsigned long long)r * (uint32_t)(c.c_hi[i] >> 32);
+    if (limb3) L3 += (unsigned long long)r * (uint32_t)(c.c_hi[i] >> 32);
   }
   L1 += L0 >> 32;
   L2 += L1 >> 32;
@@ -1183,7 +1184,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 // stored the residues of row 32 (w % 4) + lane, part w / 4 (real, imaginary).
 // With many blocks per SM the loads of the residues and of H, S overlap,
 // where the contraction's eight epilogue warps would leave the MMA waiting.
-__global__ void __launch_bounds__(256) crt_reconstruct_kernel(const __grid_constant__ GemmParams P) {
+__global__ void __launch_bounds__(256, 3) crt_reconstruct_kernel(const __grid_constant__ GemmParams P) {
   const long long t = blockIdx.x;
   const int rank = blockIdx.y, g = blockIdx.z;
   long long slot;
@@ -1202,7 +1203,7 @@ __global__ void __launch_bounds__(256) crt_reconstruct_kernel(const __grid_const
   for (int i = 0; i < kMaxModuli; ++i)
     if (i < NM)
       rv[i] = ((const uint4 *)(pr.res + ((((size_t)slot * NM + i) * 2 + rank) * 256 + threadIdx.x) * 128))[g];
-#pragma unroll
+#pragma unroll 1
   for (int u = 0; u < 16; ++u) {
     const int col = ti.n0 + g * 16 + u;
     const bool keep = col < pr.N && !(pr.uplo == 'U' && row > col) && !(pr.uplo == 'L' && row < col);
@@ -2157,6 +2158,7 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
                           slots, cw.store, pl.nmod, pl.bits, gram))
           return set_err(ctx, HSGEN_ECUDA, "split: cuTensorMapEncodeTiled failed (H/S, moduli)");
         HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s, kb0 + seg >= nkb_all));
+        if (P.recon_apart && kb0 + seg >= nkb_all) ++ctx->launches;  // crt_reconstruct_kernel
         return HSGEN_OK;
       }
       if (!hs_problems(P.prob, P.mapA, P.mapB, n_g, ldk, kb0, seg, accumulate, uplo, w.Wsl, w.Xsl, w.Ysl, w.expW,
@@ -2555,6 +2557,7 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
             P.l2_hint = ctx->l2_hint;
             P.recon_apart = ctx->crt_recon_apart;
             HSG_LAUNCH(ctx, launch_crt(P, ctx->crt_geom, s, sg == nseg - 1));
+            if (P.recon_apart && sg == nseg - 1) ++ctx->launches;  // crt_reconstruct_kernel
           } else {
             HSG_LAUNCH(ctx, launch_gemm(P, s));
           }
