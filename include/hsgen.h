@@ -109,7 +109,9 @@ typedef struct {
   int slices;               /* split form: slices per operand, 0 = from the target  */
   int uplo;                 /* 'U' (default): i <= j written; 'L': i >= j written   */
   int fill_full;            /* 1: also write the other triangle (Hermitian mirror)  */
-  int atom_chunk;           /* atoms per pass over the depth, 0 = all at once       */
+  int atom_chunk;           /* atoms per pass over the depth, 0 = the library's     */
+                            /* choice: as few passes as fit HSGEN_WS_BYTES (split   */
+                            /* form; of two, the last as large as fits), else all   */
   long long wait_timeout_ns; /* limit of every device-side wait (default 2e9)       */
   int s_form;               /* HSGEN_S_CONTRACTION (default): S = sum_a A^H A +    */
                             /* B^H U B in the chosen precision; HSGEN_S_LEGENDRE:  */

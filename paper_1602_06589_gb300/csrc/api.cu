@@ -158,8 +158,11 @@ static void free_system(hsgen_ctx *ctx) {
 static std::vector<std::pair<int, int>> atom_chunks(const hsgen_ctx *ctx) {
   int na = (int)ctx->toa.size();
   int c = ctx->opt.atom_chunk > 0 ? ctx->opt.atom_chunk : (ctx->auto_chunk > 0 ? ctx->auto_chunk : na);
+  // two uneven library-chosen passes: the first takes what the last leaves
+  const bool uneven = ctx->opt.atom_chunk <= 0 && ctx->last_chunk > 0 && ctx->last_chunk < na;
   std::vector<std::pair<int, int>> out;
   for (int a = 0; a < na; a += c) {
+    if (uneven) c = (a == 0) ? na - ctx->last_chunk : ctx->last_chunk;
     const int e = std::min(na, a + c);
     int b = a;
     for (int k = a + 1; k <= e; ++k)
@@ -704,13 +707,30 @@ hsgen_status hsgen_build_HS(hsgen_ctx *ctx, int n_g, const double *kvec, void *H
   // a6: without a caller's atom_chunk the split form takes as many atoms per
   // pass as keep its workspace within the budget (HSGEN_WS_BYTES, default 176e9)
   ctx->auto_chunk = 0;
+  ctx->last_chunk = 0;
   if (split && ctx->opt.atom_chunk <= 0) {
     double budget = 176e9;
     if (const char *e = std::getenv("HSGEN_WS_BYTES")) budget = std::max(1e6, std::atof(e));
     const int na = (int)ctx->toa.size();
-    for (int parts = 1; parts <= na; ++parts) {
+    int parts = 1;
+    for (; parts <= na; ++parts) {
       ctx->auto_chunk = (parts == 1) ? 0 : (na + parts - 1) / parts;
       if ((double)ws_layout(ctx, n_g, max_chunk_depth(ctx), split, slices).total <= budget) break;
+    }
+    // Two passes: the last one as large as the budget allows. With host
+    // outputs the finished columns leave the device while the last pass
+    // computes, so a longer last pass hides more of the copy-out.
+    if (parts == 2) {
+      int lo = ctx->auto_chunk, hi = na - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        ctx->last_chunk = mid;
+        if ((double)ws_layout(ctx, n_g, max_chunk_depth(ctx), split, slices).total <= budget)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      ctx->last_chunk = lo > ctx->auto_chunk ? lo : 0;
     }
   }
   WsLayout L = ws_layout(ctx, n_g, max_chunk_depth(ctx), split, slices);

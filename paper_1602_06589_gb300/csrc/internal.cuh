@@ -131,6 +131,7 @@ struct hsgen_ctx {
   hsg::BlockOwner owner;            // blocks of H and S the current build writes
   hsg::BlockOwner tiles_owner;      // ownership the cached tile list was built for
   int auto_chunk = 0;               // atoms per pass chosen by the library (0: all), see atom_chunk
+  int last_chunk = 0;               // two library-chosen passes: atoms of the (larger) last one, 0: equal passes
   int crt_geom = 0;                 // moduli kernel's stage geometry (0: 3 x 2 k-blocks, 1: 2 x 3)
   int crt_order = 1;                // moduli kernel's unit order (0: tile-major, 1: modulus-major)
   int l2_hint = 8;                  // moduli kernel's L2 priorities of its A and B loads (8: B evict-last)
