@@ -253,9 +253,10 @@ hsgen_status hsgen_build_HS_blocks(hsgen_ctx *ctx, int n_g, const double *kvec, 
  * n_g[k], kvec[k] (host pointers to [n_g[k]][3]), H[k], S[k] device
  * pointers with leading dimension ld[k]. The whole kernel sequence is
  * captured in a CUDA graph and replayed while sizes and pointers stay the
- * same. Slices scheme: the contraction tiles of a group of k-points (up to
- * HSGEN_BATCH_BYTES of operand planes, default 96 GiB) run in one persistent
- * launch over a grouped tile queue; moduli scheme: one k-point per group.
+ * same. The contraction tiles of a group of k-points (up to HSGEN_BATCH_BYTES
+ * of operand planes, default 96 GiB for slices and 12 GiB of residue planes
+ * and stores for moduli) run in one persistent launch over a grouped tile
+ * queue.
  * The FP64 form loops over hsgen_build_HS. */
 hsgen_status hsgen_build_HS_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double *const *kvec,
                                     void *const *H, void *const *S, const long long *ld, void *cuda_stream);

@@ -1313,84 +1313,111 @@ __global__ void __launch_bounds__(256) slice_kernel(const double2 *__restrict__ 
 // depth rows (one 4-byte store per plane).
 __constant__ float c_pow12[kMaxModuli][3];  // 2^12, 2^24, 2^36 mod m_i
 
-__global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict__ src, long long lds, int K,
-                                                      const double *__restrict__ urow, int b, CrtConsts crt,
-                                                      int planes, __nv_bfloat16 *__restrict__ dst, long long ldk,
-                                                      int ncols, long long plane_stride, int *__restrict__ expo) {
+// One output of residue_kernel: the column's values weighted by urow (or not),
+// their planes (re, im, and -re for planes == 3) and per-column exponents.
+struct ResidueOut {
+  const double *urow;
+  int planes;
+  __nv_bfloat16 *dst;
+  int *expo;
+};
+
+// One or two outputs from one read of the source column (W's residues and
+// U W's: the column is read once for both norms and once for both residues).
+__global__ void __launch_bounds__(256) residue_kernel(const double2 *__restrict__ src, long long lds, int K, int b,
+                                                      CrtConsts crt, long long ldk, int ncols, long long plane_stride,
+                                                      ResidueOut o0, ResidueOut o1, int nout) {
   const int col = blockIdx.x;
   const double2 *c = src + (size_t)col * lds;
-  __shared__ double red[8];
-  __shared__ int e_sh;
-  double ss = 0.0;  // sum of squares of the (weighted) column
+  __shared__ double red[2][8];
+  __shared__ int e_sh[2];
+  double ss[2] = {0.0, 0.0};  // sums of squares of the (weighted) column
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double2 v = c[k];
-    const double u = urow ? urow[k] : 1.0;
-    ss = fma(v.x * u, v.x * u, fma(v.y * u, v.y * u, ss));
+    const double2 v = c[k];
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      const double *urow = o ? o1.urow : o0.urow;
+      if (o < nout) {
+        const double u = urow ? urow[k] : 1.0;
+        ss[o] = fma(v.x * u, v.x * u, fma(v.y * u, v.y * u, ss[o]));
+      }
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  for (int o = 0; o < 2; ++o) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) ss[o] += __shfl_xor_sync(0xffffffffu, ss[o], d);
+    if ((threadIdx.x & 31) == 0) red[o][threadIdx.x >> 5] = ss[o];
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < (unsigned)nout) {
+    const int o = threadIdx.x;
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[o][w];
     int e = 0;
     if (t > 1e-280) {  // below: a zero column (or one that rounds to zero at any usable scale)
       const double room = ldexp(1.0, b) - 0.5 * sqrt(2.0 * (double)K);
       e = b - ilogb(room / (sqrt(t) * (1.0 + 1e-9)));
     }
-    e_sh = e;
-    expo[col] = e;
+    e_sh[o] = e;
+    (o ? o1.expo : o0.expo)[col] = e;
   }
   __syncthreads();
-  const int shift = b - e_sh;
   constexpr float kShift = 12582912.0f;  // 1.5 2^23: adding and subtracting it rounds to an integer
   for (int k = 2 * threadIdx.x; k < (int)ldk; k += 2 * blockDim.x) {  // ldk is a multiple of 64
-    // (row, re/im): |N| in four exact FP32 pieces, and the sign
-    float pc[4][4];
-    bool ng[4];
+    double2 v[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      long long N[2] = {0, 0};
-      if (k + h < K) {
-        double2 v = c[k + h];
-        if (urow) {
-          const double u = urow[k + h];
-          v.x *= u;
-          v.y *= u;
+    for (int h = 0; h < 2; ++h)
+      if (k + h < K) v[h] = c[k + h];
+    for (int o = 0; o < nout; ++o) {
+      const ResidueOut &out_o = o ? o1 : o0;
+      const int shift = b - e_sh[o];
+      // (row, re/im): |N| in four exact FP32 pieces, and the sign
+      float pc[4][4];
+      bool ng[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        long long N[2] = {0, 0};
+        if (k + h < K) {
+          double2 w = v[h];
+          if (out_o.urow) {
+            const double u = out_o.urow[k + h];
+            w.x *= u;
+            w.y *= u;
+          }
+          N[0] = to_fixed(w.x, shift);
+          N[1] = to_fixed(w.y, shift);
         }
-        N[0] = to_fixed(v.x, shift);
-        N[1] = to_fixed(v.y, shift);
-      }
 #pragma unroll
-      for (int z = 0; z < 2; ++z) {
-        const int q = 2 * z + h;
-        ng[q] = N[z] < 0;
-        const unsigned long long a = ng[q] ? (unsigned long long)(-N[z]) : (unsigned long long)N[z];
+        for (int z = 0; z < 2; ++z) {
+          const int q = 2 * z + h;
+          ng[q] = N[z] < 0;
+          const unsigned long long a = ng[q] ? (unsigned long long)(-N[z]) : (unsigned long long)N[z];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          pc[q][j] = __int_as_float(0x4B000000 | (int)((a >> (12 * j)) & 0xFFFu)) - 8388608.0f;
+          for (int j = 0; j < 4; ++j)
+            pc[q][j] = __int_as_float(0x4B000000 | (int)((a >> (12 * j)) & 0xFFFu)) - 8388608.0f;
+        }
       }
-    }
-    __nv_bfloat16 *out = dst + ((size_t)(k >> 6) * ncols + col) * 64 + (k & 63);
-    for (int i = 0; i < crt.n; ++i) {
-      const float m = (float)crt.m[i], inv = crt.inv_m[i], half = 0.5f * m;
-      const float c12 = c_pow12[i][0], c24 = c_pow12[i][1], c36 = c_pow12[i][2];
-      float r[4];
+      __nv_bfloat16 *out = out_o.dst + ((size_t)(k >> 6) * ncols + col) * 64 + (k & 63);
+      for (int i = 0; i < crt.n; ++i) {
+        const float m = (float)crt.m[i], inv = crt.inv_m[i], half = 0.5f * m;
+        const float c12 = c_pow12[i][0], c24 = c_pow12[i][1], c36 = c_pow12[i][2];
+        float r[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float a = __fmaf_rn(pc[q][3], c36, __fmaf_rn(pc[q][2], c24, __fmaf_rn(pc[q][1], c12, pc[q][0])));
-        const float qt = __fmaf_rn(a, inv, kShift) - kShift;  // a / m rounded, within one of the floor
-        float x = __fmaf_rn(-qt, m, a);                       // |N| mod m, up to one m off: |x| < 0.51 m
-        x = ng[q] ? -x : x;                                    // N mod m, up to one m off
-        x = (x > half) ? x - m : x;                            // balanced: |x| <= m / 2 <= 128
-        r[q] = (x < -half) ? x + m : x;
+        for (int q = 0; q < 4; ++q) {
+          const float a = __fmaf_rn(pc[q][3], c36, __fmaf_rn(pc[q][2], c24, __fmaf_rn(pc[q][1], c12, pc[q][0])));
+          const float qt = __fmaf_rn(a, inv, kShift) - kShift;  // a / m rounded, within one of the floor
+          float x = __fmaf_rn(-qt, m, a);                       // |N| mod m, up to one m off: |x| < 0.51 m
+          x = ng[q] ? -x : x;                                    // N mod m, up to one m off
+          x = (x > half) ? x - m : x;                            // balanced: |x| <= m / 2 <= 128
+          r[q] = (x < -half) ? x + m : x;
+        }
+        __nv_bfloat162 *base = (__nv_bfloat162 *)(out + (size_t)i * out_o.planes * plane_stride);
+        base[0] = __floats2bfloat162_rn(r[0], r[1]);  // re of rows k, k + 1
+        *(__nv_bfloat162 *)((__nv_bfloat16 *)base + plane_stride) = __floats2bfloat162_rn(r[2], r[3]);
+        if (out_o.planes == 3)
+          *(__nv_bfloat162 *)((__nv_bfloat16 *)base + 2 * plane_stride) = __floats2bfloat162_rn(-r[0], -r[1]);
       }
-      __nv_bfloat162 *base = (__nv_bfloat162 *)(out + (size_t)i * planes * plane_stride);
-      base[0] = __floats2bfloat162_rn(r[0], r[1]);  // re of rows k, k + 1
-      *(__nv_bfloat162 *)((__nv_bfloat16 *)base + plane_stride) = __floats2bfloat162_rn(r[2], r[3]);
-      if (planes == 3)
-        *(__nv_bfloat162 *)((__nv_bfloat16 *)base + 2 * plane_stride) = __floats2bfloat162_rn(-r[0], -r[1]);
     }
   }
 }
@@ -1515,7 +1542,18 @@ cudaError_t launch_residue(const double2 *src, long long lds, int K, const doubl
                            int planes, __nv_bfloat16 *dst, long long ldk, long long plane_stride, int *expo,
                            int ncols, cudaStream_t st) {
   if (ncols <= 0) return cudaSuccess;
-  residue_kernel<<<ncols, 256, 0, st>>>(src, lds, K, urow, b, crt, planes, dst, ldk, ncols, plane_stride, expo);
+  const ResidueOut o0{urow, planes, dst, expo};
+  residue_kernel<<<ncols, 256, 0, st>>>(src, lds, K, b, crt, ldk, ncols, plane_stride, o0, o0, 1);
+  return cudaGetLastError();
+}
+
+// W's residues (3 planes) and U W's (2 planes, rows weighted by urow) from one read of W.
+cudaError_t launch_residue_w_uw(const double2 *W, long long lds, int K, const double *urow, int b,
+                                const CrtConsts &crt, __nv_bfloat16 *Wr, int *expW, __nv_bfloat16 *Yr, int *expY,
+                                long long ldk, long long plane_stride, int ncols, cudaStream_t st) {
+  if (ncols <= 0) return cudaSuccess;
+  const ResidueOut o0{nullptr, 3, Wr, expW}, o1{urow, 2, Yr, expY};
+  residue_kernel<<<ncols, 256, 0, st>>>(W, lds, K, b, crt, ldk, ncols, plane_stride, o0, o1, 2);
   return cudaGetLastError();
 }
 
@@ -2092,11 +2130,11 @@ hsgen_status split_chunk(hsgen_ctx *ctx, int n_g, int a0, int a1, const double2 
   const CrtConsts cc = crt ? make_crt(pl.nmod) : CrtConsts{};
   if (crt) {
     HSG_LAUNCH(ctx, launch_residue(X, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Xr, ldk, plane, cw.expX, n_g, s));
-    if (S || !gram)
-      HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Wr, ldk, plane, cw.expW, n_g, s));
     if (S)
-      HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, ctx->d_urow + row_base, pl.bits, cc, 2, cw.Yr, ldk, plane,
-                                     cw.expY, n_g, s));
+      HSG_LAUNCH(ctx, launch_residue_w_uw(W, ldw, cdepth, ctx->d_urow + row_base, pl.bits, cc, cw.Wr, cw.expW, cw.Yr,
+                                          cw.expY, ldk, plane, n_g, s));
+    else if (!gram)
+      HSG_LAUNCH(ctx, launch_residue(W, ldw, cdepth, nullptr, pl.bits, cc, 3, cw.Wr, ldk, plane, cw.expW, n_g, s));
   } else {
     HSG_LAUNCH(ctx, launch_slice(X, ldw, cdepth, nullptr, slices, 3, w.Xsl, ldk, plane, w.expX, n_g, s));
     if (S)
@@ -2320,9 +2358,10 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
   auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
   // ---- plan: groups of k-points whose slices fit the budget
   // slices: groups of k-points up to 96 GiB of planes share each launch;
-  // moduli: one k-point per group (grouping measured slower at N_G ~3300:
-  // 8.5 ms per k-point against 7.8 for one k-point per launch)
-  size_t budget = crt ? 1 : (size_t)96 << 30;
+  // moduli: up to 12 GiB of residue planes and stores (about three k-points
+  // of N_G ~3300: 6.02 ms per k-point against 6.21 with one k-point and 6.15
+  // with eleven per launch)
+  size_t budget = (size_t)(crt ? 12 : 96) << 30;
   if (const char *e = std::getenv("HSGEN_BATCH_BYTES")) budget = (size_t)std::max(1.0, std::atof(e));
   // per k-point: 8 planes per slice or modulus (W 3, X 3, U W 2), and in the
   // moduli form its residue store (H and S tiles)
@@ -2528,11 +2567,11 @@ hsgen_status split_batched(hsgen_ctx *ctx, int n_k, const int *n_g, const double
           if (st2 != HSGEN_OK) return st2;
           if (crt) {
             HSG_LAUNCH(ctx, launch_residue(X, depth, depth, nullptr, pl.bits, cc, 3, Xsl, ldk, plane, eX, ng, s));
-            if (!leg || !gram)
-              HSG_LAUNCH(ctx, launch_residue(W, depth, depth, nullptr, pl.bits, cc, 3, Wsl, ldk, plane, eW, ng, s));
             if (!leg)
-              HSG_LAUNCH(ctx, launch_residue(W, depth, depth, ctx->d_urow, pl.bits, cc, 2, Ysl, ldk, plane, eY, ng,
-                                             s));
+              HSG_LAUNCH(ctx, launch_residue_w_uw(W, depth, depth, ctx->d_urow, pl.bits, cc, Wsl, eW, Ysl, eY, ldk,
+                                                  plane, ng, s));
+            else if (!gram)
+              HSG_LAUNCH(ctx, launch_residue(W, depth, depth, nullptr, pl.bits, cc, 3, Wsl, ldk, plane, eW, ng, s));
           } else {
             HSG_LAUNCH(ctx, launch_slice(X, depth, depth, nullptr, slices, 3, Xsl, ldk, plane, eX, ng, s));
             if (!leg)
